@@ -1,0 +1,224 @@
+/*
+ * sptrsv.h -- C ABI of the GB300 (sm_103a) sparse triangular solve library.
+ *
+ * The operations follow the paper "Reinforcement Learning-Guided Graph
+ * Transformations for SpTRSV Optimization":
+ *   - Section 2.1: the sparse triangular solve L x = b, where every row is a
+ *     node of the dependency DAG and every off-diagonal L[i][j] an edge j -> i;
+ *     the level-set method partitions the DAG into levels of independent rows.
+ *   - Section 2.2: equation rewriting, a preprocessing step that replaces a
+ *     row's dependencies by their predecessors so that it moves to an earlier
+ *     level; the result is again a CSR lower-triangular system fed to an
+ *     unchanged level-set solver.
+ *   - Section 4.1 and Tables 4-5: level costs, ALC / ARL / AIR, the coefficient
+ *     of variation of level costs and row counts and the thin-level threshold.
+ *   - Related work (synchronisation-free solves): rows start as soon as their
+ *     own predecessors are done, with lightweight flags instead of barriers.
+ *
+ * Conventions for every call:
+ *   - A matrix is CSR with int32 row_ptr[n+1] and col_idx[nnz]; columns of a
+ *     row strictly increase, all are < i except the last, which is the
+ *     diagonal i; the diagonal is non-zero.  Values are FP64 or FP32.
+ *   - Array arguments are DEVICE pointers owned by the caller unless stated
+ *     otherwise; the library never frees them.  Host scalars/outputs are
+ *     marked "(host)".
+ *   - Dense right-hand sides and solutions are [n x nrhs] row-major with
+ *     leading dimension ld >= nrhs (elements), in the matrix's value type.
+ *   - Every call returns a status code and never throws.  Work is enqueued on
+ *     the handle's stream; calls return before the GPU finishes unless they
+ *     say they synchronise.  Faults found by the GPU (e.g. a bounded wait that
+ *     gave up) are recorded in a device status word and returned by
+ *     sptrsv_get_status().
+ *   - A plan keeps pointers to the caller's matrix arrays; they must stay
+ *     valid and unmodified in structure for the plan's lifetime (values may
+ *     change between solves).
+ */
+#ifndef SPTRSV_GB300_H
+#define SPTRSV_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SPTRSV_OK = 0,
+    SPTRSV_EINVAL = 1,     /* bad argument (null pointer, size, row index)   */
+    SPTRSV_ENOTLOWER = 2,  /* a column > i, or < 0                           */
+    SPTRSV_EDIAG = 3,      /* diagonal missing, not last, or zero            */
+    SPTRSV_EUNSORTED = 4,  /* columns of a row not strictly increasing       */
+    SPTRSV_ETARGET = 5,    /* rewrite target t < 0 or t >= lev(i), lev(i)==0 */
+    SPTRSV_ENOMEM = 6,     /* device allocation failed                       */
+    SPTRSV_ETIMEOUT = 7,   /* a bounded device wait gave up                  */
+    SPTRSV_ECUDA = 8,      /* a CUDA runtime call failed                     */
+    SPTRSV_ENOTSUP = 9     /* option not supported for this input            */
+} sptrsv_status;
+
+typedef enum { SPTRSV_F64 = 0, SPTRSV_F32 = 1 } sptrsv_dtype;
+
+/* Matrix descriptor (device pointers, caller-owned). */
+typedef struct {
+    int32_t n;
+    int64_t nnz;
+    const int32_t *row_ptr;
+    const int32_t *col_idx;
+    const void *vals;
+    sptrsv_dtype dtype;
+} sptrsv_csr;
+
+/* Writable descriptor used for rewrite outputs (device pointers). */
+typedef struct {
+    int32_t *row_ptr;  /* n+1 */
+    int32_t *col_idx;  /* nnz */
+    void *vals;        /* nnz, same dtype as the input */
+} sptrsv_csr_out;
+
+typedef enum {
+    SPTRSV_MODE_AUTO = 0,
+    /* Plain level-set solve (Section 2.1): one kernel launch per level,
+     * one thread per row.  This is the baseline the other modes must beat. */
+    SPTRSV_MODE_LEVEL_LAUNCH = 1,
+    /* Level-set solve in ONE persistent launch: warps take row groups in
+     * level order and wait on a grid-wide progress counter for the previous
+     * level instead of a launch boundary.                                    */
+    SPTRSV_MODE_LEVEL_PERSISTENT = 2,
+    /* Synchronisation-free solve: row groups taken in row order, each row
+     * waits on its own predecessors' ready flags (acquire/release).          */
+    SPTRSV_MODE_SYNCFREE = 3,
+    /* Synchronisation-free solve inside one thread block: flags and recent
+     * solution values live in shared memory; for deep, narrow systems where
+     * the cross-SM flag round trip would dominate.                           */
+    SPTRSV_MODE_BLOCK = 4
+} sptrsv_mode;
+
+typedef struct {
+    int32_t mode;            /* sptrsv_mode; AUTO picks from the level profile */
+    int32_t rows_per_warp;   /* 1,2,4,8,16,32 (lanes per row = 32/rows_per_warp); 0 = auto */
+    int32_t rhs_tile;        /* right-hand sides per pass: 1,2,4,8,16; 0 = auto */
+    int32_t build_transpose; /* non-zero: prepare sptrsv_solve_transpose / grad  */
+    int64_t spin_limit;      /* polls before a device wait gives up; 0 = default */
+} sptrsv_plan_opts;
+
+typedef struct sptrsv_handle_st *sptrsv_handle;
+typedef struct sptrsv_plan_st *sptrsv_plan;
+
+/* ------------------------------------------------------------------ handle */
+/* Creates a handle bound to the current CUDA device and to `stream` (a
+ * cudaStream_t; NULL = the legacy default stream).                         */
+sptrsv_status sptrsv_create(sptrsv_handle *handle, void *stream);
+sptrsv_status sptrsv_destroy(sptrsv_handle handle);
+sptrsv_status sptrsv_set_stream(sptrsv_handle handle, void *stream);
+/* Synchronises the stream, returns the first error any kernel recorded since
+ * the last call (SPTRSV_OK if none) and clears it.                          */
+sptrsv_status sptrsv_get_status(sptrsv_handle handle);
+const char *sptrsv_status_string(sptrsv_status status);
+
+/* ---------------------------------------------------------------- validate */
+/* Checks that L is a lower-triangular CSR with sorted columns and a non-zero
+ * diagonal stored last (Section 2.1).  Synchronises.  On failure returns the
+ * code of the first offending row in row order and writes that row to
+ * *bad_row (host, may be NULL).                                             */
+sptrsv_status sptrsv_validate(sptrsv_handle handle, const sptrsv_csr *L, int32_t *bad_row);
+
+/* ----------------------------------------------------------------- analyze */
+/* Level-set analysis of L (Section 2.1; level table and costs of Section 4.1):
+ *   lev[i]        level of row i: 0 without off-diagonals, else
+ *                 1 + max over predecessors (longest path from a source);
+ *   perm[n]       rows sorted by (level, row);
+ *   level_ptr[]   level l occupies perm[level_ptr[l] .. level_ptr[l+1]);
+ *                 caller allocates n+1 entries (worst case);
+ *   level_cost[]  sum over the level's rows of 2*offdiag(i)+1 (int64);
+ *                 caller allocates n entries (worst case);
+ *   *nlevels      (host) number of levels;
+ *   stats[6]      (host) ALC, ARL, AIR, CV of level costs, CV of rows per
+ *                 level (population), thin threshold ALC*(1+max(0,1-CV)).
+ * Validates L first (codes as sptrsv_validate).  Synchronises.              */
+sptrsv_status sptrsv_analyze(sptrsv_handle handle, const sptrsv_csr *L, int32_t *lev,
+                             int32_t *perm, int32_t *level_ptr, int64_t *level_cost,
+                             int32_t *nlevels, double stats[6]);
+
+/* ----------------------------------------------------------------- rewrite */
+/* Equation rewriting (Section 2.2) by row substitution.  rows[q] (device,
+ * nrows entries) is rewritten towards target level targets[q] (device; NULL
+ * means lev(i)-1): every predecessor j with lev(j) >= t is replaced, largest
+ * column first, by row j's own predecessors with coefficients scaled by
+ * m = acc[j] / L_jj, using the ORIGINAL rows and the ORIGINAL levels `lev`
+ * (device, from sptrsv_analyze).  The result is L' (same n) and T (n rows,
+ * no diagonal) with L' x = b + T b.  A row listed twice keeps its smallest
+ * target.  Two-phase: with Lp_out == NULL the call only computes the sizes
+ * (*nnz_Lp, *nnz_T, host); call again with buffers of those sizes.  Both
+ * phases synchronise.  Errors: SPTRSV_EINVAL for a row outside [0, n),
+ * SPTRSV_ETARGET for a target outside [0, lev(i)) or lev(i) == 0.           */
+sptrsv_status sptrsv_rewrite(sptrsv_handle handle, const sptrsv_csr *L, const int32_t *lev,
+                             const int32_t *rows, const int32_t *targets, int32_t nrows,
+                             int64_t *nnz_Lp, int64_t *nnz_T,
+                             sptrsv_csr_out *Lp_out, sptrsv_csr_out *T_out);
+
+/* ------------------------------------------------------------------- solve */
+/* Builds a reusable solve plan for L (and, for a rewritten system, T: the
+ * solve then computes x = L^{-1} (b + T b), the T gather fused into the rows
+ * that have one).  Runs the level analysis internally and synchronises.
+ * opts may be NULL (defaults).                                              */
+sptrsv_status sptrsv_plan_create(sptrsv_handle handle, const sptrsv_csr *L, const sptrsv_csr *T,
+                                 const sptrsv_plan_opts *opts, sptrsv_plan *plan);
+sptrsv_status sptrsv_plan_destroy(sptrsv_plan plan);
+/* (host outputs, each may be NULL) number of levels of the plan's schedule,
+ * the mode, rows per warp and rhs tile the plan uses.                       */
+sptrsv_status sptrsv_plan_info(sptrsv_plan plan, int32_t *nlevels, int32_t *mode,
+                               int32_t *rows_per_warp, int32_t *rhs_tile);
+/* Changes the mode / rows per warp / rhs tile of an existing plan (used by
+ * the autotuner); builds whatever schedule data the new mode needs.         */
+sptrsv_status sptrsv_plan_set(sptrsv_plan plan, int32_t mode, int32_t rows_per_warp,
+                              int32_t rhs_tile);
+
+/* x = L^{-1} b  (or L^{-1} (b + T b)).  Asynchronous.  b and x must not
+ * overlap.                                                                  */
+sptrsv_status sptrsv_solve(sptrsv_plan plan, const void *b, void *x, int32_t nrhs, int64_t ld);
+
+/* Adjoint of the solve: g_b = L^{-T} g_x, processed in reverse level /
+ * reverse row order.  Requires build_transpose.  Asynchronous.              */
+sptrsv_status sptrsv_solve_transpose(sptrsv_plan plan, const void *gx, void *gb, int32_t nrhs,
+                                     int64_t ld);
+
+/* Value gradient on L's pattern: gvals[p] = -sum_r gb[i,r] * x[j,r] for the
+ * stored entry p = (i, j), diagonal included.  Asynchronous.                */
+sptrsv_status sptrsv_grad_vals(sptrsv_plan plan, const void *gb, const void *x, int32_t nrhs,
+                               int64_t ld, void *gvals);
+
+/* Adjoint of b -> b + T b for a rewritten plan: gb = gbp + T^T gbp.        */
+sptrsv_status sptrsv_tt_apply(sptrsv_plan plan, const void *gbp, void *gb, int32_t nrhs,
+                              int64_t ld);
+
+/* ----------------------------------------------------------------- batched */
+/* One plan over nmat independent systems (Ls, Ts, nrhs: host arrays of nmat
+ * entries; Ts may be NULL or hold entries with n == 0 for "no T"; opts may
+ * be NULL or an array of nmat per-matrix options).  All matrices share the
+ * dtype of Ls[0].  Right-hand sides, solutions and gradients are PACKED:
+ * matrix m's [n_m x nrhs_m] block (ld = nrhs_m) starts at element
+ * rhs_offset[m] of one buffer, its value gradient at vals_offset[m];
+ * sptrsv_batch_offsets returns both (host arrays of nmat+1 entries).        */
+sptrsv_status sptrsv_batch_plan_create(sptrsv_handle handle, int32_t nmat, const sptrsv_csr *Ls,
+                                       const sptrsv_csr *Ts, const int32_t *nrhs,
+                                       const sptrsv_plan_opts *opts, sptrsv_plan *plan);
+sptrsv_status sptrsv_batch_offsets(sptrsv_plan plan, int64_t *rhs_offset, int64_t *vals_offset);
+/* All systems in one persistent launch (plus a tiny reset launch): no host
+ * work per matrix, so the call can be captured in a CUDA graph.            */
+sptrsv_status sptrsv_batch_solve(sptrsv_plan plan, const void *b, void *x);
+sptrsv_status sptrsv_batch_solve_transpose(sptrsv_plan plan, const void *gx, void *gb);
+sptrsv_status sptrsv_batch_grad_vals(sptrsv_plan plan, const void *gb, const void *x,
+                                     void *gvals);
+sptrsv_status sptrsv_batch_tt_apply(sptrsv_plan plan, const void *gbp, void *gb);
+
+/* ------------------------------------------------------------- diagnostics */
+/* Test hook for the bounded waits: makes the next solves of `plan` skip
+ * publishing row `row` (-1 clears it), so that any row waiting on it gives
+ * up after spin_limit polls and the solve reports SPTRSV_ETIMEOUT.          */
+sptrsv_status sptrsv_debug_withhold_row(sptrsv_plan plan, int32_t row);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPTRSV_GB300_H */

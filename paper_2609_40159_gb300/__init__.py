@@ -1,0 +1,16 @@
+"""GB300-native (sm_103a) sparse triangular solve over the dependency DAG.
+
+Level-set analysis, equation rewriting, level-scheduled / synchronisation-free
+/ block-local solves, batched solves and their adjoints, all in hand-written
+CUDA behind the C ABI of include/sptrsv.h.  Importing the package does not
+touch the GPU; the first call that needs the library loads
+``libsptrsv_gb300.so`` and raises if it has not been built.
+"""
+from . import _lib
+from .api import Analysis, BatchPlan, Handle, Matrix, Plan, analyze, handle, rewrite, validate
+from .autograd import BatchSpTRSVFunction, SpTRSVFunction, batch_solve, solve
+
+__all__ = [
+    "_lib", "Analysis", "BatchPlan", "Handle", "Matrix", "Plan", "analyze", "handle", "rewrite",
+    "validate", "SpTRSVFunction", "BatchSpTRSVFunction", "solve", "batch_solve",
+]

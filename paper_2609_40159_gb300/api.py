@@ -1,0 +1,314 @@
+"""Torch-facing wrappers over the C ABI: argument marshalling only.
+
+PyTorch provides device memory and streams; every step of the solve path
+runs in the library's CUDA kernels.  All calls use the current CUDA stream.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import _lib as L
+
+_DTYPES = {torch.float64: L.SPTRSV_F64, torch.float32: L.SPTRSV_F32}
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None and t.numel() > 0 else C.c_void_p(0)
+
+
+class Matrix:
+    """Lower-triangular CSR matrix in device memory (int32 indices, FP64 or
+    FP32 values), the diagonal stored last in every row."""
+
+    def __init__(self, row_ptr: torch.Tensor, col_idx: torch.Tensor, vals: torch.Tensor):
+        if row_ptr.dtype != torch.int32 or col_idx.dtype != torch.int32:
+            raise TypeError("row_ptr and col_idx must be int32")
+        if vals.dtype not in _DTYPES:
+            raise TypeError("vals must be float64 or float32")
+        for t in (row_ptr, col_idx, vals):
+            if not t.is_cuda:
+                raise ValueError("matrix arrays must live on a CUDA device")
+            if not t.is_contiguous():
+                raise ValueError("matrix arrays must be contiguous")
+        self.row_ptr, self.col_idx, self.vals = row_ptr, col_idx, vals
+        self.n = row_ptr.numel() - 1
+        self.nnz = col_idx.numel()
+        if vals.numel() != self.nnz:
+            raise ValueError("vals and col_idx differ in length")
+
+    @property
+    def dtype(self):
+        return self.vals.dtype
+
+    @classmethod
+    def from_host(cls, A, device="cuda", dtype=None):
+        """From any object with n, row_ptr, col_idx, vals numpy arrays."""
+        vals = torch.as_tensor(np.ascontiguousarray(A.vals))
+        if dtype is not None:
+            vals = vals.to(dtype)
+        return cls(torch.as_tensor(np.ascontiguousarray(A.row_ptr, dtype=np.int32)).to(device),
+                   torch.as_tensor(np.ascontiguousarray(A.col_idx, dtype=np.int32)).to(device),
+                   vals.to(device))
+
+    def desc(self) -> L.sptrsv_csr:
+        return L.sptrsv_csr(self.n, self.nnz, _ptr(self.row_ptr), _ptr(self.col_idx),
+                            _ptr(self.vals), _DTYPES[self.vals.dtype])
+
+    def to_host(self):
+        return (self.row_ptr.cpu().numpy(), self.col_idx.cpu().numpy(), self.vals.cpu().numpy())
+
+
+class Handle:
+    """Library handle bound to one CUDA stream."""
+
+    def __init__(self, stream: torch.cuda.Stream | None = None):
+        s = stream if stream is not None else torch.cuda.current_stream()
+        self.stream = s
+        h = L.sptrsv_handle()
+        L.check(L.lib().sptrsv_create(C.byref(h), C.c_void_p(s.cuda_stream)), "sptrsv_create")
+        self.h = h
+
+    def status(self) -> int:
+        """Synchronise and return (and clear) the device status word."""
+        return int(L.lib().sptrsv_get_status(self.h))
+
+    def __del__(self):
+        try:
+            if getattr(self, "h", None):
+                L.lib().sptrsv_destroy(self.h)
+        except Exception:
+            pass
+
+
+_handles: dict = {}
+
+
+def handle() -> Handle:
+    """Handle for the current device and stream (cached)."""
+    s = torch.cuda.current_stream()
+    key = (s.device.index, s.cuda_stream)
+    h = _handles.get(key)
+    if h is None:
+        h = Handle(s)
+        _handles[key] = h
+    return h
+
+
+def validate(A: Matrix):
+    """(status, first offending row or -1); see sptrsv_validate."""
+    bad = C.c_int32(-1)
+    st = L.lib().sptrsv_validate(handle().h, C.byref(A.desc()), C.byref(bad))
+    return int(st), int(bad.value)
+
+
+@dataclass
+class Analysis:
+    lev: torch.Tensor        # [n] int32
+    perm: torch.Tensor       # [n] int32
+    level_ptr: torch.Tensor  # [nlevels+1] int32
+    cost: torch.Tensor       # [nlevels] int64
+    nlevels: int
+    stats: np.ndarray        # ALC, ARL, AIR, CV(cost), CV(rows), thin threshold
+
+    STAT_NAMES = ("alc", "arl", "air", "cv_cost", "cv_rows", "thin_threshold")
+
+
+def analyze(A: Matrix) -> Analysis:
+    dev = A.row_ptr.device
+    n = A.n
+    lev = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+    perm = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+    lp = torch.empty(n + 1, dtype=torch.int32, device=dev)
+    cost = torch.empty(max(n, 1), dtype=torch.int64, device=dev)
+    nl = C.c_int32(0)
+    st = (C.c_double * 6)()
+    L.check(L.lib().sptrsv_analyze(handle().h, C.byref(A.desc()), _ptr(lev), _ptr(perm), _ptr(lp),
+                                   _ptr(cost), C.byref(nl), st), "sptrsv_analyze")
+    k = int(nl.value)
+    return Analysis(lev[:n], perm[:n], lp[:k + 1], cost[:k], k, np.array(list(st)))
+
+
+def rewrite(A: Matrix, lev: torch.Tensor, rows, targets=None):
+    """Row-substitution rewrite (see sptrsv_rewrite); returns (L', T)."""
+    dev = A.row_ptr.device
+    rows = torch.as_tensor(rows, dtype=torch.int32).to(dev).contiguous()
+    tg = None if targets is None else torch.as_tensor(targets, dtype=torch.int32).to(dev).contiguous()
+    nlp, nt = C.c_int64(0), C.c_int64(0)
+    lp_rp = torch.empty(A.n + 1, dtype=torch.int32, device=dev)
+    t_rp = torch.empty(A.n + 1, dtype=torch.int32, device=dev)
+    h = handle().h
+    desc = A.desc()
+    lib = L.lib()
+    L.check(lib.sptrsv_rewrite(h, C.byref(desc), _ptr(lev), _ptr(rows), _ptr(tg), int(rows.numel()),
+                               C.byref(nlp), C.byref(nt), None, None), "sptrsv_rewrite (sizes)")
+    lp_ci = torch.empty(max(nlp.value, 1), dtype=torch.int32, device=dev)
+    lp_v = torch.empty(max(nlp.value, 1), dtype=A.dtype, device=dev)
+    t_ci = torch.empty(max(nt.value, 1), dtype=torch.int32, device=dev)
+    t_v = torch.empty(max(nt.value, 1), dtype=A.dtype, device=dev)
+    o1 = L.sptrsv_csr_out(_ptr(lp_rp), _ptr(lp_ci), _ptr(lp_v))
+    o2 = L.sptrsv_csr_out(_ptr(t_rp), _ptr(t_ci), _ptr(t_v))
+    L.check(lib.sptrsv_rewrite(h, C.byref(desc), _ptr(lev), _ptr(rows), _ptr(tg), int(rows.numel()),
+                               C.byref(nlp), C.byref(nt), C.byref(o1), C.byref(o2)), "sptrsv_rewrite")
+    Lp = Matrix(lp_rp, lp_ci[: nlp.value], lp_v[: nlp.value])
+    T = Matrix(t_rp, t_ci[: nt.value], t_v[: nt.value])
+    return Lp, T
+
+
+class Plan:
+    """Reusable solve plan for L (and T of a rewritten system)."""
+
+    def __init__(self, A: Matrix, T: Matrix | None = None, mode="auto", rows_per_warp=0,
+                 rhs_tile=0, transpose=False, spin_limit=0):
+        self.A, self.T = A, T
+        opts = L.sptrsv_plan_opts(L.MODE_NAMES[mode] if isinstance(mode, str) else int(mode),
+                                  rows_per_warp, rhs_tile, 1 if transpose else 0, spin_limit)
+        p = L.sptrsv_plan()
+        self._h = handle()
+        tdesc = T.desc() if T is not None else None
+        L.check(L.lib().sptrsv_plan_create(self._h.h, C.byref(A.desc()),
+                                           C.byref(tdesc) if tdesc is not None else None,
+                                           C.byref(opts), C.byref(p)), "sptrsv_plan_create")
+        self.p = p
+
+    def info(self):
+        nl, m, r, k = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
+        L.check(L.lib().sptrsv_plan_info(self.p, C.byref(nl), C.byref(m), C.byref(r), C.byref(k)))
+        return dict(nlevels=nl.value, mode=m.value, rows_per_warp=r.value, rhs_tile=k.value)
+
+    def set(self, mode=0, rows_per_warp=0, rhs_tile=0):
+        mode = L.MODE_NAMES[mode] if isinstance(mode, str) else int(mode)
+        L.check(L.lib().sptrsv_plan_set(self.p, mode, rows_per_warp, rhs_tile), "sptrsv_plan_set")
+
+    def withhold(self, row: int):
+        L.check(L.lib().sptrsv_debug_withhold_row(self.p, row))
+
+    @staticmethod
+    def _rhs(b, n, dtype):
+        if b.dim() == 1:
+            b = b.view(n, 1)
+        if b.dtype != dtype or not b.is_cuda or b.shape[0] != n or b.stride(1) != 1:
+            raise ValueError("right-hand side must be an [n, k] CUDA tensor of the matrix dtype "
+                             "with unit column stride")
+        return b
+
+    def solve(self, b: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        squeeze = b.dim() == 1
+        b2 = self._rhs(b, self.A.n, self.A.dtype)
+        x = out if out is not None else torch.empty(self.A.n, b2.shape[1], dtype=b2.dtype, device=b2.device)
+        x2 = self._rhs(x, self.A.n, self.A.dtype)
+        L.check(L.lib().sptrsv_solve(self.p, _ptr(b2), _ptr(x2), b2.shape[1], b2.stride(0)),
+                "sptrsv_solve")
+        return x.view(-1) if squeeze and out is None else x
+
+    def solve_transpose(self, gx: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        squeeze = gx.dim() == 1
+        g2 = self._rhs(gx, self.A.n, self.A.dtype)
+        gb = out if out is not None else torch.empty(self.A.n, g2.shape[1], dtype=g2.dtype, device=g2.device)
+        L.check(L.lib().sptrsv_solve_transpose(self.p, _ptr(g2), _ptr(gb), g2.shape[1], g2.stride(0)),
+                "sptrsv_solve_transpose")
+        return gb.view(-1) if squeeze and out is None else gb
+
+    def grad_vals(self, gb: torch.Tensor, x: torch.Tensor, out: torch.Tensor | None = None):
+        gb2 = self._rhs(gb, self.A.n, self.A.dtype)
+        x2 = self._rhs(x, self.A.n, self.A.dtype)
+        gv = out if out is not None else torch.empty(self.A.nnz, dtype=self.A.dtype, device=gb2.device)
+        L.check(L.lib().sptrsv_grad_vals(self.p, _ptr(gb2), _ptr(x2), gb2.shape[1], gb2.stride(0),
+                                         _ptr(gv)), "sptrsv_grad_vals")
+        return gv
+
+    def tt_apply(self, gbp: torch.Tensor, out: torch.Tensor | None = None):
+        squeeze = gbp.dim() == 1
+        g2 = self._rhs(gbp, self.A.n, self.A.dtype)
+        gb = out if out is not None else torch.empty_like(g2)
+        L.check(L.lib().sptrsv_tt_apply(self.p, _ptr(g2), _ptr(gb), g2.shape[1], g2.stride(0)),
+                "sptrsv_tt_apply")
+        return gb.view(-1) if squeeze and out is None else gb
+
+    def __del__(self):
+        try:
+            if getattr(self, "p", None):
+                L.lib().sptrsv_plan_destroy(self.p)
+        except Exception:
+            pass
+
+
+class BatchPlan:
+    """One plan over many independent systems; right-hand sides, solutions
+    and gradients are packed (see sptrsv_batch_plan_create)."""
+
+    def __init__(self, mats, Ts=None, nrhs=None, rows_per_warp=None, transpose=False, spin_limit=0):
+        nmat = len(mats)
+        self.mats, self.Ts = list(mats), list(Ts) if Ts is not None else [None] * nmat
+        self.nrhs = [int(k) for k in (nrhs if nrhs is not None else [1] * nmat)]
+        descs = (L.sptrsv_csr * max(nmat, 1))()
+        tdescs = (L.sptrsv_csr * max(nmat, 1))()
+        opts = (L.sptrsv_plan_opts * max(nmat, 1))()
+        for m, A in enumerate(self.mats):
+            descs[m] = A.desc()
+            T = self.Ts[m]
+            tdescs[m] = T.desc() if T is not None else L.sptrsv_csr(0, 0, None, None, None, 0)
+            rpw = 0 if rows_per_warp is None else int(rows_per_warp[m] if hasattr(rows_per_warp, "__len__") else rows_per_warp)
+            opts[m] = L.sptrsv_plan_opts(L.SPTRSV_MODE_BLOCK, rpw, 0, 1 if transpose else 0, spin_limit)
+        ks = (C.c_int32 * max(nmat, 1))(*self.nrhs)
+        self._h = handle()
+        p = L.sptrsv_plan()
+        L.check(L.lib().sptrsv_batch_plan_create(self._h.h, nmat, descs, tdescs, ks, opts, C.byref(p)),
+                "sptrsv_batch_plan_create")
+        self.p = p
+        ro = (C.c_int64 * (nmat + 1))()
+        vo = (C.c_int64 * (nmat + 1))()
+        L.check(L.lib().sptrsv_batch_offsets(p, ro, vo))
+        self.rhs_offset = np.array(list(ro), dtype=np.int64)
+        self.vals_offset = np.array(list(vo), dtype=np.int64)
+        self.dtype = mats[0].dtype if nmat else torch.float32
+
+    @property
+    def total_rhs(self):
+        return int(self.rhs_offset[-1])
+
+    @property
+    def total_nnz(self):
+        return int(self.vals_offset[-1])
+
+    def _check(self, t, size):
+        if t.dtype != self.dtype or not t.is_cuda or t.numel() != size or not t.is_contiguous():
+            raise ValueError(f"packed buffer must be a contiguous CUDA {self.dtype} tensor of {size} elements")
+
+    def solve(self, b, out=None):
+        self._check(b, self.total_rhs)
+        x = out if out is not None else torch.empty_like(b)
+        L.check(L.lib().sptrsv_batch_solve(self.p, _ptr(b), _ptr(x)), "sptrsv_batch_solve")
+        return x
+
+    def solve_transpose(self, gx, out=None):
+        self._check(gx, self.total_rhs)
+        gb = out if out is not None else torch.empty_like(gx)
+        L.check(L.lib().sptrsv_batch_solve_transpose(self.p, _ptr(gx), _ptr(gb)), "sptrsv_batch_solve_transpose")
+        return gb
+
+    def grad_vals(self, gb, x, out=None):
+        self._check(gb, self.total_rhs)
+        gv = out if out is not None else torch.empty(self.total_nnz, dtype=self.dtype, device=gb.device)
+        L.check(L.lib().sptrsv_batch_grad_vals(self.p, _ptr(gb), _ptr(x), _ptr(gv)), "sptrsv_batch_grad_vals")
+        return gv
+
+    def tt_apply(self, gbp, out=None):
+        self._check(gbp, self.total_rhs)
+        gb = out if out is not None else torch.empty_like(gbp)
+        L.check(L.lib().sptrsv_batch_tt_apply(self.p, _ptr(gbp), _ptr(gb)), "sptrsv_batch_tt_apply")
+        return gb
+
+    def unpack(self, packed, m):
+        a, b = int(self.rhs_offset[m]), int(self.rhs_offset[m + 1])
+        return packed[a:b].view(self.mats[m].n, self.nrhs[m])
+
+    def __del__(self):
+        try:
+            if getattr(self, "p", None):
+                L.lib().sptrsv_plan_destroy(self.p)
+        except Exception:
+            pass

@@ -1,0 +1,323 @@
+// Level-set analysis on the GPU (paper Section 2.1; level table, level costs
+// and their statistics of Section 4.1 / Tables 4-5).
+//
+//   validate  -- one warp per row: lower triangular, sorted, diagonal last.
+//   levels    -- lev[i] = 0 without predecessors, else 1 + max lev[j]; computed
+//                as a synchronisation-free max-plus "solve": warps take chunks
+//                of 32 consecutive rows from a ticket counter (so every chunk
+//                only waits on chunks already taken by running warps), rows
+//                inside the chunk resolve through shared memory, rows of
+//                earlier chunks are polled in global memory with bounded waits.
+//   hist      -- rows and costs per level (2*offdiag+1 per row, int64).
+//   stats     -- ALC, ARL, AIR and the coefficients of variation from exact
+//                integer sums (the m*S2 - S1^2 difference in 128 bits, rounded
+//                to double once), so that they are reproducible bit for bit.
+//   partition -- perm = rows sorted by (level, row): stable radix sort by level.
+#include <climits>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace spt {
+
+namespace {
+
+// ------------------------------------------------------------- validation
+__global__ void k_validate(const int32_t *rp, const int32_t *ci, const void *vals, int dtype,
+                           int32_t n, int64_t nnz, long long *out)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t ii = gw; ii < n; ii += nw) {
+        const int32_t i = (int32_t)ii;
+        const int32_t a = rp[i], e = rp[i + 1];
+        int code = 0;
+        if (i == 0 && a != 0) code = SPTRSV_EINVAL;
+        else if (a < 0 || e > nnz || e < a) code = SPTRSV_EINVAL;
+        else if (e == a) code = SPTRSV_EDIAG;
+        if (code == 0) {
+            // first offending position in row order decides between
+            // "outside [0, i]" and "not strictly increasing"
+            int first_code = 0;
+            for (int p0 = a; p0 < e; p0 += 32) {
+                const int p = p0 + lane;
+                int c = 0;
+                if (p < e) {
+                    const int32_t col = ci[p];
+                    if (col < 0 || col > i) c = SPTRSV_ENOTLOWER;
+                    else if (p > a && col <= ci[p - 1]) c = SPTRSV_EUNSORTED;
+                }
+                const unsigned bad = __ballot_sync(SPT_FULL_MASK, c != 0);
+                if (bad) {
+                    const int src = __ffs(bad) - 1;
+                    first_code = __shfl_sync(SPT_FULL_MASK, c, src);
+                    break;
+                }
+            }
+            code = first_code;
+            if (code == 0) {
+                const bool zero = dtype == SPTRSV_F64 ? ((const double *)vals)[e - 1] == 0.0
+                                                      : ((const float *)vals)[e - 1] == 0.0f;
+                if (ci[e - 1] != i || zero) code = SPTRSV_EDIAG;
+            }
+        }
+        if (code != 0 && lane == 0) atomicMin(out, (long long)i * 16 + code);
+    }
+}
+
+// ----------------------------------------------------------------- levels
+constexpr int kLevThreads = 256;
+constexpr int kLevWarps = kLevThreads / 32;
+
+__global__ void __launch_bounds__(kLevThreads)
+k_levels(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, int32_t n, int32_t *lev,
+         unsigned long long *ticket, Waiter w)
+{
+    __shared__ int slev[kLevWarps][32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    volatile int *my = slev[wid];
+    for (;;) {
+        unsigned long long c = 0;
+        if (lane == 0) c = atomicAdd(ticket, 1ull);
+        c = __shfl_sync(SPT_FULL_MASK, c, 0);
+        const int64_t base = (int64_t)c * 32;
+        if (base >= n) return;
+        const int64_t i = base + lane;
+        const bool valid = i < n;
+        int p = valid ? ldro(rp + i) : 0;
+        const int pend = valid ? ldro(rp + i + 1) - 1 : 0;
+        int m = -1;
+        bool done = !valid, failed = false;
+        my[lane] = -1;
+        __syncwarp();
+        for (;;) {
+            if (!done) {
+                while (p < pend) {
+                    const int32_t j = ldro(ci + p);
+                    int lj;
+                    if (j >= base) {
+                        lj = my[j - base];
+                        if (lj < 0) break;  // produced by this warp later
+                    } else {
+                        lj = ld_relaxed(lev + j);
+                        if (lj < 0) {
+                            long long polls = 0;
+                            for (;;) {
+                                lj = ld_relaxed(lev + j);
+                                if (lj >= 0) break;
+                                if ((++polls & 255) == 0) {
+                                    if (aborted(w)) { failed = true; break; }
+                                    if (polls >= w.limit) { give_up(w); failed = true; break; }
+                                }
+                            }
+                            if (failed) break;
+                        }
+                    }
+                    m = m > lj ? m : lj;
+                    ++p;
+                }
+                if (failed) done = true;
+                else if (p >= pend) {
+                    const int lv = m + 1;
+                    my[lane] = lv;
+                    st_relaxed(lev + i, lv);
+                    done = true;
+                }
+            }
+            __syncwarp();
+            if (__any_sync(SPT_FULL_MASK, failed)) return;
+            if (__all_sync(SPT_FULL_MASK, done)) break;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- max/hist
+__global__ void k_max(const int32_t *lev, int32_t n, int32_t *out)
+{
+    int m = -1;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        m = max(m, lev[i]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(SPT_FULL_MASK, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, m);
+}
+
+__global__ void k_level_hist(const int32_t *rp, const int32_t *lev, int32_t n, int32_t *counts,
+                             unsigned long long *cost)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int l = lev[i];
+        atomicAdd(counts + l, 1);
+        atomicAdd(cost + l, (unsigned long long)(2 * (rp[i + 1] - rp[i] - 1) + 1));
+    }
+}
+
+__global__ void k_iota(int32_t *v, int32_t n)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        v[i] = (int32_t)i;
+}
+
+// ------------------------------------------------------------------ stats
+typedef unsigned __int128 u128;
+
+// Correctly rounded u128 -> double: keep the top 64 bits with the discarded
+// bits folded into a sticky bit, round those once, scale by a power of two.
+__device__ double u128_to_double_rn(u128 v)
+{
+    const unsigned long long hi = (unsigned long long)(v >> 64);
+    if (hi == 0) return __ull2double_rn((unsigned long long)v);
+    const int bits = 128 - __clzll((long long)hi);  // > 64
+    const int shift = bits - 64;
+    unsigned long long top = (unsigned long long)(v >> shift);
+    const u128 rest = v & ((((u128)1) << shift) - 1);
+    if (rest != 0) top |= 1ull;
+    const double t = __ull2double_rn(top);
+    return t * __longlong_as_double((long long)(1023 + shift) << 52);
+}
+
+__device__ double cov_exact(long long m, long long S1, u128 S2)
+{
+    if (m <= 0 || S1 <= 0) return 0.0;
+    const u128 a = (u128)(unsigned long long)m * S2;
+    const u128 b = (u128)(unsigned long long)S1 * (u128)(unsigned long long)S1;
+    const u128 d = a > b ? a - b : (u128)0;
+    return __ddiv_rn(__dsqrt_rn(u128_to_double_rn(d)), __ll2double_rn(S1));
+}
+
+__global__ void __launch_bounds__(512)
+k_level_stats(int32_t n, int64_t nnz, int32_t nlevels, const int32_t *level_ptr,
+              const int64_t *cost, double *out)
+{
+    __shared__ long long s1[512], r1[512];
+    __shared__ u128 s2[512], r2[512];
+    long long a1 = 0, b1 = 0;
+    u128 a2 = 0, b2 = 0;
+    for (int l = threadIdx.x; l < nlevels; l += blockDim.x) {
+        const unsigned long long c = (unsigned long long)cost[l];
+        const unsigned long long r = (unsigned long long)(level_ptr[l + 1] - level_ptr[l]);
+        a1 += (long long)c;
+        a2 += (u128)c * c;
+        b1 += (long long)r;
+        b2 += (u128)r * r;
+    }
+    s1[threadIdx.x] = a1; s2[threadIdx.x] = a2;
+    r1[threadIdx.x] = b1; r2[threadIdx.x] = b2;
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    long long S1 = 0, R1 = 0;
+    u128 S2 = 0, R2 = 0;
+    for (int t = 0; t < (int)blockDim.x; ++t) {
+        S1 += s1[t]; S2 += s2[t]; R1 += r1[t]; R2 += r2[t];
+    }
+    for (int q = 0; q < 6; ++q) out[q] = 0.0;
+    if (n <= 0 || nlevels <= 0) return;
+    const double L = (double)nlevels;
+    const double alc = __ddiv_rn(__ll2double_rn(S1), L);
+    out[0] = alc;
+    out[1] = __ddiv_rn((double)n, L);
+    out[2] = __ddiv_rn(__ll2double_rn(nnz - (long long)n), (double)n);
+    const double cv = cov_exact(nlevels, S1, S2);
+    out[3] = cv;
+    out[4] = cov_exact(nlevels, R1, R2);
+    double relax = __dsub_rn(1.0, cv);
+    if (relax < 0.0) relax = 0.0;
+    out[5] = __dmul_rn(alc, __dadd_rn(1.0, relax));
+}
+
+int grid_for(int64_t work, int threads, int cap = 65535 * 4)
+{
+    int64_t b = (work + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > cap) b = cap;
+    return (int)b;
+}
+
+}  // namespace
+
+cudaError_t launch_validate(const sptrsv_csr &L, long long *out_dev, cudaStream_t s)
+{
+    long long init = LLONG_MAX;
+    cudaError_t e = cudaMemcpyAsync(out_dev, &init, sizeof(init), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return e;
+    if (L.n <= 0) return cudaSuccess;
+    k_validate<<<grid_for((int64_t)L.n * 32, 256), 256, 0, s>>>(L.row_ptr, L.col_idx, L.vals,
+                                                                (int)L.dtype, L.n, L.nnz, out_dev);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_levels(const sptrsv_csr &L, int32_t *lev, const Ctl &ctl, long long spin_limit,
+                          const DeviceInfo &di, cudaStream_t s)
+{
+    if (L.n <= 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(ctl.counters, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_levels, kLevThreads, 0);
+    if (per_sm < 1) per_sm = 1;
+    const int64_t chunks = ((int64_t)L.n + 31) / 32;
+    int64_t blocks = (int64_t)per_sm * di.num_sms;
+    const int64_t need = (chunks + kLevWarps - 1) / kLevWarps;
+    if (blocks > need) blocks = need;
+    Waiter w{ctl.status, ctl.abort_flag, spin_limit};
+    k_levels<<<(int)blocks, kLevThreads, 0, s>>>(L.row_ptr, L.col_idx, L.n, lev, ctl.counters, w);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_max(const int32_t *lev, int32_t n, int32_t *maxlev_dev, cudaStream_t s)
+{
+    int init = -1;
+    cudaError_t e = cudaMemcpyAsync(maxlev_dev, &init, sizeof(int), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess || n <= 0) return e;
+    k_max<<<grid_for(n, 256, 1024), 256, 0, s>>>(lev, n, maxlev_dev);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_level_hist(const sptrsv_csr &L, const int32_t *lev, int32_t nlevels,
+                              int32_t *counts, int64_t *cost, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(int32_t) * (size_t)nlevels, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(cost, 0, sizeof(int64_t) * (size_t)nlevels, s);
+    if (e != cudaSuccess || L.n <= 0) return e;
+    k_level_hist<<<grid_for(L.n, 256), 256, 0, s>>>(L.row_ptr, lev, L.n, counts,
+                                                    (unsigned long long *)cost);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_level_stats(int32_t n, int64_t nnz, int32_t nlevels, const int32_t *level_ptr,
+                               const int64_t *cost, double *stats_dev, cudaStream_t s)
+{
+    k_level_stats<<<1, 512, 0, s>>>(n, nnz, nlevels, level_ptr, cost, stats_dev);
+    return cudaGetLastError();
+}
+
+cudaError_t level_partition(const sptrsv_csr &L, const int32_t *lev, int32_t nlevels,
+                            int32_t *perm, int32_t *level_ptr, int64_t *cost, cudaStream_t s)
+{
+    const int32_t n = L.n;
+    if (n <= 0) return cudaMemsetAsync(level_ptr, 0, sizeof(int32_t), s);
+    int32_t *counts = nullptr, *iota = nullptr;
+    uint32_t *keys_out = nullptr;
+    cudaError_t e = cudaMallocAsync(&counts, sizeof(int32_t) * (size_t)nlevels, s);
+    if (e == cudaSuccess) e = cudaMallocAsync(&iota, sizeof(int32_t) * (size_t)n, s);
+    if (e == cudaSuccess) e = cudaMallocAsync(&keys_out, sizeof(uint32_t) * (size_t)n, s);
+    if (e != cudaSuccess) return e;
+    e = launch_level_hist(L, lev, nlevels, counts, cost, s);
+    if (e == cudaSuccess) e = exclusive_scan_i32(counts, level_ptr, nlevels, nullptr, s);
+    if (e == cudaSuccess) {
+        k_iota<<<grid_for(n, 256), 256, 0, s>>>(iota, n);
+        int bits = 0;
+        while (bits < 32 && ((uint32_t)(nlevels - 1) >> bits) != 0) ++bits;
+        e = radix_sort_pairs((const uint32_t *)lev, iota, keys_out, perm, n, bits, s);
+    }
+    cudaFreeAsync(counts, s);
+    cudaFreeAsync(iota, s);
+    cudaFreeAsync(keys_out, s);
+    return e;
+}
+
+}  // namespace spt

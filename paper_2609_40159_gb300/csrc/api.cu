@@ -1,0 +1,681 @@
+// C ABI of the SpTRSV library (declared in include/sptrsv.h): handles, plans,
+// level analysis, rewriting, single and batched solves, adjoints.
+#include <algorithm>
+#include <climits>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <vector>
+
+#include "solve.cuh"
+
+using namespace spt;
+
+namespace {
+constexpr long long kDefaultSpin = 1ll << 22;
+
+sptrsv_status from_cuda(cudaError_t e)
+{
+    if (e == cudaSuccess) return SPTRSV_OK;
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? SPTRSV_ENOMEM : SPTRSV_ECUDA;
+}
+
+int default_rpw(int32_t n, int64_t nnz)
+{
+    const double avg = n > 0 ? (double)nnz / n : 1.0;
+    if (avg <= 12) return 32;
+    if (avg <= 24) return 16;
+    if (avg <= 48) return 8;
+    if (avg <= 96) return 4;
+    return 1;
+}
+
+int default_kt(int k)
+{
+    int kt = 1;
+    while (kt < k && kt < 16) kt <<= 1;
+    return kt;
+}
+
+bool valid_rpw(int r) { return r == 1 || r == 2 || r == 4 || r == 8 || r == 16 || r == 32; }
+bool valid_kt(int k) { return k == 1 || k == 2 || k == 4 || k == 8 || k == 16; }
+}  // namespace
+
+struct sptrsv_handle_st {
+    cudaStream_t stream = nullptr;
+    DeviceInfo di;
+    int *d_status = nullptr;
+    PlanCtl *d_ctl = nullptr;
+    long long *d_scratch = nullptr;  // validation result, max level, stats
+};
+
+struct PlanMat {
+    // one system of a (possibly batched) plan
+    sptrsv_csr L{};
+    sptrsv_csr T{};
+    bool hasT = false;
+    int32_t nlevels = 0;
+    int32_t *d_lev = nullptr, *d_perm = nullptr, *d_level_ptr = nullptr;
+    std::vector<int32_t> h_level_ptr;
+    int32_t *d_cp = nullptr, *d_crow = nullptr, *d_tmap = nullptr;
+    uint32_t *d_tmask = nullptr;
+};
+
+struct sptrsv_plan_st {
+    sptrsv_handle h = nullptr;
+    bool batched = false;
+    sptrsv_dtype dtype = SPTRSV_F64;
+    long long spin = kDefaultSpin;
+    int32_t withhold = -1;
+    bool have_csc = false;
+    std::vector<void *> owned;
+    PlanCtl *d_ctl = nullptr;
+    // single system
+    PlanMat M;
+    int mode = SPTRSV_MODE_SYNCFREE, rpw = 32, kt = 1;
+    int32_t *d_chunk_fwd = nullptr, *d_chunk_tr = nullptr;
+    int chunk_rpw = 0;
+    uint32_t *d_flags = nullptr;
+    int grid_level = 0, grid_sf = 0;
+    // batched
+    std::vector<PlanMat> mats;
+    std::vector<int64_t> rhs_off, vals_off, row_off;
+    BatchMat *d_mats = nullptr;
+    int32_t *d_order = nullptr;
+    int64_t *d_row_off = nullptr;
+    size_t batch_smem = 0;
+    int batch_grid_sz = 0;
+
+    template <class P> cudaError_t alloc(P **p, size_t bytes)
+    {
+        void *q = nullptr;
+        cudaError_t e = cudaMalloc(&q, bytes > 0 ? bytes : 16);
+        if (e == cudaSuccess) { owned.push_back(q); *p = static_cast<P *>(q); }
+        return e;
+    }
+};
+
+// ------------------------------------------------------------------ handle
+extern "C" sptrsv_status sptrsv_create(sptrsv_handle *handle, void *stream)
+{
+    if (!handle) return SPTRSV_EINVAL;
+    *handle = nullptr;
+    sptrsv_handle h = new (std::nothrow) sptrsv_handle_st;
+    if (!h) return SPTRSV_ENOMEM;
+    h->stream = (cudaStream_t)stream;
+    cudaError_t e = cudaGetDevice(&h->di.device);
+    int sms = 0, smem = 0;
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->di.device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->di.device);
+    h->di.num_sms = sms;
+    h->di.max_smem_optin = (size_t)smem;
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_status, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_ctl, sizeof(PlanCtl));
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_scratch, 16 * sizeof(long long));
+    if (e == cudaSuccess) e = cudaMemset(h->d_status, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(h->d_ctl, 0, sizeof(PlanCtl));
+    if (e != cudaSuccess) {
+        cudaFree(h->d_status); cudaFree(h->d_ctl); cudaFree(h->d_scratch);
+        delete h;
+        return from_cuda(e);
+    }
+    *handle = h;
+    return SPTRSV_OK;
+}
+
+extern "C" sptrsv_status sptrsv_destroy(sptrsv_handle h)
+{
+    if (!h) return SPTRSV_EINVAL;
+    cudaStreamSynchronize(h->stream);
+    cudaFree(h->d_status);
+    cudaFree(h->d_ctl);
+    cudaFree(h->d_scratch);
+    delete h;
+    return SPTRSV_OK;
+}
+
+extern "C" sptrsv_status sptrsv_set_stream(sptrsv_handle h, void *stream)
+{
+    if (!h) return SPTRSV_EINVAL;
+    h->stream = (cudaStream_t)stream;
+    return SPTRSV_OK;
+}
+
+extern "C" sptrsv_status sptrsv_get_status(sptrsv_handle h)
+{
+    if (!h) return SPTRSV_EINVAL;
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return from_cuda(e);
+    int st = 0;
+    e = cudaMemcpy(&st, h->d_status, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return from_cuda(e);
+    if (st != 0) cudaMemset(h->d_status, 0, sizeof(int));
+    return (sptrsv_status)st;
+}
+
+extern "C" const char *sptrsv_status_string(sptrsv_status s)
+{
+    switch (s) {
+    case SPTRSV_OK: return "ok";
+    case SPTRSV_EINVAL: return "invalid argument";
+    case SPTRSV_ENOTLOWER: return "matrix is not lower triangular";
+    case SPTRSV_EDIAG: return "diagonal missing, not last or zero";
+    case SPTRSV_EUNSORTED: return "columns of a row are not strictly increasing";
+    case SPTRSV_ETARGET: return "rewrite target outside [0, lev(i))";
+    case SPTRSV_ENOMEM: return "out of device memory";
+    case SPTRSV_ETIMEOUT: return "a bounded device wait gave up";
+    case SPTRSV_ECUDA: return "CUDA error";
+    case SPTRSV_ENOTSUP: return "not supported";
+    }
+    return "unknown status";
+}
+
+// -------------------------------------------------------------- internals
+namespace {
+
+sptrsv_status check_csr(const sptrsv_csr *L)
+{
+    if (!L || L->n < 0 || L->nnz < 0 || L->nnz >= INT_MAX) return SPTRSV_EINVAL;
+    if (L->dtype != SPTRSV_F64 && L->dtype != SPTRSV_F32) return SPTRSV_EINVAL;
+    if (L->n > 0 && (!L->row_ptr || !L->col_idx || !L->vals)) return SPTRSV_EINVAL;
+    return SPTRSV_OK;
+}
+
+sptrsv_status validate_impl(sptrsv_handle h, const sptrsv_csr &L, int32_t *bad_row)
+{
+    if (bad_row) *bad_row = -1;
+    if (L.n == 0) return SPTRSV_OK;
+    cudaError_t e = launch_validate(L, h->d_scratch, h->stream);
+    long long r = LLONG_MAX;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&r, h->d_scratch, sizeof(r), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return from_cuda(e);
+    if (r == LLONG_MAX) return SPTRSV_OK;
+    if (bad_row) *bad_row = (int32_t)(r / 16);
+    return (sptrsv_status)(r % 16);
+}
+
+// Levels of L into lev (device, n) and their count.  Validates first.
+sptrsv_status levels_impl(sptrsv_handle h, const sptrsv_csr &L, int32_t *lev, int32_t *nlevels,
+                          long long spin)
+{
+    *nlevels = 0;
+    sptrsv_status st = validate_impl(h, L, nullptr);
+    if (st != SPTRSV_OK || L.n == 0) return st;
+    cudaStream_t s = h->stream;
+    cudaError_t e = cudaMemsetAsync(lev, 0xFF, sizeof(int32_t) * (size_t)L.n, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(&h->d_ctl->abort_flag, 0, sizeof(int), s);
+    Ctl ctl{h->d_status, &h->d_ctl->abort_flag, &h->d_ctl->ticket};
+    if (e == cudaSuccess) e = launch_levels(L, lev, ctl, spin, h->di, s);
+    int32_t *dmax = reinterpret_cast<int32_t *>(h->d_scratch + 1);
+    if (e == cudaSuccess) e = launch_max(lev, L.n, dmax, s);
+    int32_t hm = -1;
+    int hab = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hm, dmax, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hab, &h->d_ctl->abort_flag, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return from_cuda(e);
+    if (hab) return SPTRSV_ETIMEOUT;
+    *nlevels = hm + 1;
+    return SPTRSV_OK;
+}
+
+sptrsv_status analyze_into(sptrsv_handle h, const sptrsv_csr &L, int32_t *lev, int32_t *perm,
+                           int32_t *level_ptr, int64_t *cost, int32_t *nlevels, double *stats,
+                           long long spin)
+{
+    sptrsv_status st = levels_impl(h, L, lev, nlevels, spin);
+    if (st != SPTRSV_OK) return st;
+    cudaStream_t s = h->stream;
+    cudaError_t e = level_partition(L, lev, *nlevels, perm, level_ptr, cost, s);
+    if (e == cudaSuccess && stats) {
+        double *dst = reinterpret_cast<double *>(h->d_scratch + 2);
+        e = launch_level_stats(L.n, L.nnz, *nlevels, level_ptr, cost, dst, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(stats, dst, 6 * sizeof(double), cudaMemcpyDeviceToHost, s);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    return from_cuda(e);
+}
+
+template <class T> Sys<T> sys_of(const PlanMat &M)
+{
+    Sys<T> A;
+    A.n = M.L.n;
+    A.rp = M.L.row_ptr; A.ci = M.L.col_idx; A.v = (const T *)M.L.vals;
+    A.cp = M.d_cp; A.crow = M.d_crow; A.tmap = M.d_tmap;
+    A.trp = M.hasT ? M.T.row_ptr : nullptr;
+    A.tci = M.hasT ? M.T.col_idx : nullptr;
+    A.tv = M.hasT ? (const T *)M.T.vals : nullptr;
+    A.tmask = M.hasT ? M.d_tmask : nullptr;
+    return A;
+}
+
+// Analysis + schedule data + optional CSC for one system of a plan.
+sptrsv_status prepare_mat(sptrsv_plan p, PlanMat &M, const sptrsv_csr &L, const sptrsv_csr *T,
+                          bool want_csc)
+{
+    sptrsv_handle h = p->h;
+    cudaStream_t s = h->stream;
+    M.L = L;
+    const int32_t n = L.n;
+    const size_t nn = (size_t)(n > 0 ? n : 1);
+    if (T && T->n > 0) {
+        if (T->n != n || T->dtype != L.dtype || !T->row_ptr || (T->nnz > 0 && (!T->col_idx || !T->vals)))
+            return SPTRSV_EINVAL;
+        M.T = *T;
+        M.hasT = true;
+    }
+    cudaError_t e = p->alloc(&M.d_lev, sizeof(int32_t) * nn);
+    if (e == cudaSuccess) e = p->alloc(&M.d_perm, sizeof(int32_t) * nn);
+    if (e == cudaSuccess) e = p->alloc(&M.d_level_ptr, sizeof(int32_t) * (nn + 1));
+    int64_t *cost = nullptr;
+    if (e == cudaSuccess) e = cudaMalloc(&cost, sizeof(int64_t) * nn);
+    if (e != cudaSuccess) { cudaFree(cost); return from_cuda(e); }
+    sptrsv_status st = analyze_into(h, L, M.d_lev, M.d_perm, M.d_level_ptr, cost, &M.nlevels, nullptr, p->spin);
+    cudaFree(cost);
+    if (st != SPTRSV_OK) return st;
+    M.h_level_ptr.assign((size_t)M.nlevels + 1, 0);
+    if (n > 0) {
+        e = cudaMemcpy(M.h_level_ptr.data(), M.d_level_ptr, sizeof(int32_t) * (M.nlevels + 1), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return from_cuda(e);
+    }
+    if (M.hasT) {
+        e = p->alloc(&M.d_tmask, sizeof(uint32_t) * ((nn + 31) / 32));
+        if (e == cudaSuccess) e = build_tmask(M.T.row_ptr, n, M.d_tmask, s);
+        if (e != cudaSuccess) return from_cuda(e);
+    }
+    if (want_csc) {
+        e = p->alloc(&M.d_cp, sizeof(int32_t) * (nn + 1));
+        if (e == cudaSuccess) e = p->alloc(&M.d_crow, sizeof(int32_t) * (size_t)(L.nnz > 0 ? L.nnz : 1));
+        if (e == cudaSuccess) e = p->alloc(&M.d_tmap, sizeof(int32_t) * (size_t)(L.nnz > 0 ? L.nnz : 1));
+        if (e == cudaSuccess) e = build_csc(L.row_ptr, L.col_idx, n, L.nnz, M.d_cp, M.d_crow, M.d_tmap, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return from_cuda(e);
+    }
+    return SPTRSV_OK;
+}
+
+sptrsv_status ensure_chunks(sptrsv_plan p)
+{
+    if (p->chunk_rpw == p->rpw) return SPTRSV_OK;
+    const int32_t n = p->M.L.n;
+    const int64_t nch = ((int64_t)n + p->rpw - 1) / p->rpw;
+    cudaError_t e = cudaSuccess;
+    // chunk tables are owned; reallocate at the largest size ever needed
+    if (!p->d_chunk_fwd) {
+        const int64_t maxch = n > 0 ? n : 1;  // rpw = 1
+        e = p->alloc(&p->d_chunk_fwd, sizeof(int32_t) * (size_t)maxch);
+        if (e == cudaSuccess) e = p->alloc(&p->d_chunk_tr, sizeof(int32_t) * (size_t)maxch);
+        if (e != cudaSuccess) return from_cuda(e);
+    }
+    if (nch > 0 && p->M.nlevels > 0) {
+        e = build_chunk_levels(p->M.d_level_ptr, p->M.nlevels, n, p->rpw, false, p->d_chunk_fwd, p->h->stream);
+        if (e == cudaSuccess)
+            e = build_chunk_levels(p->M.d_level_ptr, p->M.nlevels, n, p->rpw, true, p->d_chunk_tr, p->h->stream);
+        if (e != cudaSuccess) return from_cuda(e);
+    }
+    p->chunk_rpw = p->rpw;
+    return SPTRSV_OK;
+}
+
+int auto_mode(const PlanMat &M)
+{
+    if (M.L.n == 0 || M.nlevels == 0) return SPTRSV_MODE_SYNCFREE;
+    const double width = (double)M.L.n / M.nlevels;
+    if (width < 48.0) return SPTRSV_MODE_BLOCK;
+    return SPTRSV_MODE_SYNCFREE;
+}
+
+template <class T>
+sptrsv_status solve_impl(sptrsv_plan p, const void *b, void *x, int32_t nrhs, int64_t ld, bool trans)
+{
+    const PlanMat &M = p->M;
+    if (M.L.n == 0) return SPTRSV_OK;
+    if (!b || !x || nrhs < 1 || ld < nrhs) return SPTRSV_EINVAL;
+    if (trans && !p->have_csc) return SPTRSV_ENOTSUP;
+    cudaStream_t s = p->h->stream;
+    Sys<T> A = sys_of<T>(M);
+    Rhs<T> R{(const T *)b, (T *)x, ld, nrhs};
+    SyncArgs sy{p->d_flags, p->d_ctl, p->withhold, Waiter{p->h->d_status, &p->d_ctl->abort_flag, p->spin}};
+    const int kt = std::min(p->kt, default_kt(nrhs));
+    cudaError_t e = cudaSuccess;
+    int mode = p->mode;
+    if (mode == SPTRSV_MODE_BLOCK && !block_mode_supported(nrhs, sizeof(T) == 8)) mode = SPTRSV_MODE_SYNCFREE;
+    switch (mode) {
+    case SPTRSV_MODE_LEVEL_LAUNCH:
+        e = solve_level_launch<T>(A, M.d_perm, M.h_level_ptr, R, trans, s);
+        break;
+    case SPTRSV_MODE_LEVEL_PERSISTENT: {
+        sptrsv_status st = ensure_chunks(p);
+        if (st != SPTRSV_OK) return st;
+        Sched S{M.d_perm, M.d_level_ptr, M.nlevels, trans ? p->d_chunk_tr : p->d_chunk_fwd,
+                ((int64_t)M.L.n + p->rpw - 1) / p->rpw};
+        e = solve_level_persistent<T>(A, S, R, p->rpw, kt, trans, sy, p->grid_level, s);
+        break;
+    }
+    case SPTRSV_MODE_BLOCK:
+        e = solve_block<T>(A, R, p->rpw, kt, trans, sy, s);
+        break;
+    default:
+        e = solve_syncfree<T>(A, R, p->rpw, kt, trans, sy, p->grid_sf, s);
+        break;
+    }
+    return from_cuda(e);
+}
+
+}  // namespace
+
+// --------------------------------------------------------------- validate
+extern "C" sptrsv_status sptrsv_validate(sptrsv_handle h, const sptrsv_csr *L, int32_t *bad_row)
+{
+    if (!h) return SPTRSV_EINVAL;
+    sptrsv_status st = check_csr(L);
+    if (st != SPTRSV_OK) return st;
+    return validate_impl(h, *L, bad_row);
+}
+
+// ---------------------------------------------------------------- analyze
+extern "C" sptrsv_status sptrsv_analyze(sptrsv_handle h, const sptrsv_csr *L, int32_t *lev,
+                                        int32_t *perm, int32_t *level_ptr, int64_t *level_cost,
+                                        int32_t *nlevels, double stats[6])
+{
+    if (!h || !nlevels) return SPTRSV_EINVAL;
+    sptrsv_status st = check_csr(L);
+    if (st != SPTRSV_OK) return st;
+    if (L->n > 0 && (!lev || !perm || !level_ptr || !level_cost)) return SPTRSV_EINVAL;
+    if (L->n == 0) {
+        *nlevels = 0;
+        if (stats) for (int q = 0; q < 6; ++q) stats[q] = 0.0;
+        if (level_ptr) cudaMemsetAsync(level_ptr, 0, sizeof(int32_t), h->stream);
+        return from_cuda(cudaStreamSynchronize(h->stream));
+    }
+    double tmp[6];
+    return analyze_into(h, *L, lev, perm, level_ptr, level_cost, nlevels, stats ? stats : tmp, kDefaultSpin);
+}
+
+// ---------------------------------------------------------------- rewrite
+extern "C" sptrsv_status sptrsv_rewrite(sptrsv_handle h, const sptrsv_csr *L, const int32_t *lev,
+                                        const int32_t *rows, const int32_t *targets, int32_t nrows,
+                                        int64_t *nnz_Lp, int64_t *nnz_T, sptrsv_csr_out *Lp_out,
+                                        sptrsv_csr_out *T_out)
+{
+    if (!h || nrows < 0) return SPTRSV_EINVAL;
+    sptrsv_status st = check_csr(L);
+    if (st != SPTRSV_OK) return st;
+    if (L->n > 0 && !lev) return SPTRSV_EINVAL;
+    if (nrows > 0 && !rows) return SPTRSV_EINVAL;
+    return (sptrsv_status)rewrite_run(*L, lev, rows, targets, nrows, nnz_Lp, nnz_T, Lp_out, T_out,
+                                      h->di, h->stream);
+}
+
+// ------------------------------------------------------------------ plans
+extern "C" sptrsv_status sptrsv_plan_create(sptrsv_handle h, const sptrsv_csr *L, const sptrsv_csr *T,
+                                            const sptrsv_plan_opts *opts, sptrsv_plan *plan)
+{
+    if (!h || !plan) return SPTRSV_EINVAL;
+    *plan = nullptr;
+    sptrsv_status st = check_csr(L);
+    if (st != SPTRSV_OK) return st;
+    sptrsv_plan p = new (std::nothrow) sptrsv_plan_st;
+    if (!p) return SPTRSV_ENOMEM;
+    p->h = h;
+    p->dtype = L->dtype;
+    sptrsv_plan_opts o{};
+    if (opts) o = *opts;
+    if (o.spin_limit > 0) p->spin = o.spin_limit;
+    cudaError_t e = p->alloc(&p->d_ctl, sizeof(PlanCtl));
+    if (e == cudaSuccess) e = cudaMemset(p->d_ctl, 0, sizeof(PlanCtl));
+    if (e == cudaSuccess) e = p->alloc(&p->d_flags, sizeof(uint32_t) * (size_t)(L->n > 0 ? L->n : 1));
+    if (e == cudaSuccess) e = cudaMemset(p->d_flags, 0, sizeof(uint32_t) * (size_t)(L->n > 0 ? L->n : 1));
+    if (e != cudaSuccess) { sptrsv_plan_destroy(p); return from_cuda(e); }
+    st = prepare_mat(p, p->M, *L, T, o.build_transpose != 0);
+    if (st != SPTRSV_OK) { sptrsv_plan_destroy(p); return st; }
+    p->have_csc = o.build_transpose != 0;
+    p->mode = o.mode != SPTRSV_MODE_AUTO ? o.mode : auto_mode(p->M);
+    p->rpw = valid_rpw(o.rows_per_warp) ? o.rows_per_warp : default_rpw(L->n, L->nnz);
+    p->kt = valid_kt(o.rhs_tile) ? o.rhs_tile : 16;
+    if (p->mode < SPTRSV_MODE_LEVEL_LAUNCH || p->mode > SPTRSV_MODE_BLOCK) { sptrsv_plan_destroy(p); return SPTRSV_EINVAL; }
+    p->grid_level = persistent_grid_level(1, p->dtype == SPTRSV_F64, h->di);
+    p->grid_sf = persistent_grid_syncfree(1, p->dtype == SPTRSV_F64, h->di);
+    st = ensure_chunks(p);
+    if (st == SPTRSV_OK) st = from_cuda(cudaStreamSynchronize(h->stream));
+    if (st != SPTRSV_OK) { sptrsv_plan_destroy(p); return st; }
+    *plan = p;
+    return SPTRSV_OK;
+}
+
+extern "C" sptrsv_status sptrsv_plan_destroy(sptrsv_plan p)
+{
+    if (!p) return SPTRSV_EINVAL;
+    if (p->h) cudaStreamSynchronize(p->h->stream);
+    for (void *q : p->owned) cudaFree(q);
+    delete p;
+    return SPTRSV_OK;
+}
+
+extern "C" sptrsv_status sptrsv_plan_info(sptrsv_plan p, int32_t *nlevels, int32_t *mode,
+                                          int32_t *rows_per_warp, int32_t *rhs_tile)
+{
+    if (!p) return SPTRSV_EINVAL;
+    if (nlevels) {
+        if (p->batched) {
+            int32_t mx = 0;
+            for (const PlanMat &M : p->mats) mx = std::max(mx, M.nlevels);
+            *nlevels = mx;
+        } else {
+            *nlevels = p->M.nlevels;
+        }
+    }
+    if (mode) *mode = p->batched ? SPTRSV_MODE_BLOCK : p->mode;
+    if (rows_per_warp) *rows_per_warp = p->rpw;
+    if (rhs_tile) *rhs_tile = p->kt;
+    return SPTRSV_OK;
+}
+
+extern "C" sptrsv_status sptrsv_plan_set(sptrsv_plan p, int32_t mode, int32_t rows_per_warp, int32_t rhs_tile)
+{
+    if (!p || p->batched) return SPTRSV_EINVAL;
+    if (mode < SPTRSV_MODE_AUTO || mode > SPTRSV_MODE_BLOCK) return SPTRSV_EINVAL;
+    if (rows_per_warp != 0 && !valid_rpw(rows_per_warp)) return SPTRSV_EINVAL;
+    if (rhs_tile != 0 && !valid_kt(rhs_tile)) return SPTRSV_EINVAL;
+    p->mode = mode == SPTRSV_MODE_AUTO ? auto_mode(p->M) : mode;
+    if (rows_per_warp) p->rpw = rows_per_warp;
+    if (rhs_tile) p->kt = rhs_tile;
+    sptrsv_status st = ensure_chunks(p);
+    if (st != SPTRSV_OK) return st;
+    return from_cuda(cudaStreamSynchronize(p->h->stream));
+}
+
+extern "C" sptrsv_status sptrsv_solve(sptrsv_plan p, const void *b, void *x, int32_t nrhs, int64_t ld)
+{
+    if (!p || p->batched) return SPTRSV_EINVAL;
+    return p->dtype == SPTRSV_F64 ? solve_impl<double>(p, b, x, nrhs, ld, false)
+                                  : solve_impl<float>(p, b, x, nrhs, ld, false);
+}
+
+extern "C" sptrsv_status sptrsv_solve_transpose(sptrsv_plan p, const void *gx, void *gb, int32_t nrhs, int64_t ld)
+{
+    if (!p || p->batched) return SPTRSV_EINVAL;
+    return p->dtype == SPTRSV_F64 ? solve_impl<double>(p, gx, gb, nrhs, ld, true)
+                                  : solve_impl<float>(p, gx, gb, nrhs, ld, true);
+}
+
+extern "C" sptrsv_status sptrsv_grad_vals(sptrsv_plan p, const void *gb, const void *x, int32_t nrhs,
+                                          int64_t ld, void *gvals)
+{
+    if (!p || p->batched) return SPTRSV_EINVAL;
+    if (p->M.L.n == 0) return SPTRSV_OK;
+    if (!gb || !x || !gvals || nrhs < 1 || ld < nrhs) return SPTRSV_EINVAL;
+    cudaError_t e;
+    if (p->dtype == SPTRSV_F64)
+        e = grad_vals<double>(sys_of<double>(p->M), (const double *)gb, (const double *)x, ld, nrhs, (double *)gvals, p->h->stream);
+    else
+        e = grad_vals<float>(sys_of<float>(p->M), (const float *)gb, (const float *)x, ld, nrhs, (float *)gvals, p->h->stream);
+    return from_cuda(e);
+}
+
+extern "C" sptrsv_status sptrsv_tt_apply(sptrsv_plan p, const void *gbp, void *gb, int32_t nrhs, int64_t ld)
+{
+    if (!p || p->batched) return SPTRSV_EINVAL;
+    if (p->M.L.n == 0) return SPTRSV_OK;
+    if (!gbp || !gb || nrhs < 1 || ld < nrhs) return SPTRSV_EINVAL;
+    cudaError_t e;
+    if (p->dtype == SPTRSV_F64)
+        e = tt_apply<double>(sys_of<double>(p->M), (const double *)gbp, (double *)gb, ld, nrhs, p->h->stream);
+    else
+        e = tt_apply<float>(sys_of<float>(p->M), (const float *)gbp, (float *)gb, ld, nrhs, p->h->stream);
+    return from_cuda(e);
+}
+
+extern "C" sptrsv_status sptrsv_debug_withhold_row(sptrsv_plan p, int32_t row)
+{
+    if (!p) return SPTRSV_EINVAL;
+    p->withhold = row;
+    return SPTRSV_OK;
+}
+
+// ----------------------------------------------------------------- batched
+extern "C" sptrsv_status sptrsv_batch_plan_create(sptrsv_handle h, int32_t nmat, const sptrsv_csr *Ls,
+                                                  const sptrsv_csr *Ts, const int32_t *nrhs,
+                                                  const sptrsv_plan_opts *opts, sptrsv_plan *plan)
+{
+    if (!h || !plan || nmat < 0 || (nmat > 0 && (!Ls || !nrhs))) return SPTRSV_EINVAL;
+    *plan = nullptr;
+    sptrsv_plan p = new (std::nothrow) sptrsv_plan_st;
+    if (!p) return SPTRSV_ENOMEM;
+    p->h = h;
+    p->batched = true;
+    p->dtype = nmat > 0 ? Ls[0].dtype : SPTRSV_F32;
+    p->have_csc = false;
+    bool want_csc = false;
+    for (int m = 0; m < nmat && opts; ++m) want_csc = want_csc || opts[m].build_transpose;
+    if (opts && opts[0].spin_limit > 0) p->spin = opts[0].spin_limit;
+    cudaError_t e = p->alloc(&p->d_ctl, sizeof(PlanCtl));
+    if (e == cudaSuccess) e = cudaMemset(p->d_ctl, 0, sizeof(PlanCtl));
+    if (e != cudaSuccess) { sptrsv_plan_destroy(p); return from_cuda(e); }
+    p->mats.resize((size_t)nmat);
+    p->rhs_off.assign((size_t)nmat + 1, 0);
+    p->vals_off.assign((size_t)nmat + 1, 0);
+    p->row_off.assign((size_t)nmat + 1, 0);
+    std::vector<BatchMat> hm((size_t)nmat);
+    std::vector<double> est((size_t)nmat);
+    size_t smem = 16;
+    const bool f64 = p->dtype == SPTRSV_F64;
+    for (int m = 0; m < nmat; ++m) {
+        sptrsv_status st = check_csr(&Ls[m]);
+        if (st == SPTRSV_OK && (Ls[m].dtype != p->dtype || nrhs[m] < 1 || !block_mode_supported(nrhs[m], f64)))
+            st = nrhs[m] < 1 || Ls[m].dtype != p->dtype ? SPTRSV_EINVAL : SPTRSV_ENOTSUP;
+        if (st == SPTRSV_OK) st = prepare_mat(p, p->mats[m], Ls[m], Ts ? &Ts[m] : nullptr, want_csc);
+        if (st != SPTRSV_OK) { sptrsv_plan_destroy(p); return st; }
+        const PlanMat &M = p->mats[m];
+        BatchMat &B = hm[m];
+        B.n = M.L.n;
+        B.k = nrhs[m];
+        const int orpw = opts ? opts[m].rows_per_warp : 0;
+        B.rpw = valid_rpw(orpw) ? orpw : default_rpw(M.L.n, M.L.nnz);
+        B.kt = block_kt_for(B.k);
+        block_geometry(B.rpw, B.kt, f64, &B.kc, &B.P);
+        smem = std::max(smem, block_smem_bytes(B.rpw, B.kt, B.kc, f64));
+        B.nnz = M.L.nnz;
+        B.rp = M.L.row_ptr; B.ci = M.L.col_idx; B.v = M.L.vals;
+        B.cp = M.d_cp; B.crow = M.d_crow; B.tmap = M.d_tmap;
+        B.trp = M.hasT ? M.T.row_ptr : nullptr;
+        B.tci = M.hasT ? M.T.col_idx : nullptr;
+        B.tv = M.hasT ? M.T.vals : nullptr;
+        B.tmask = M.hasT ? M.d_tmask : nullptr;
+        B.rhs_off = p->rhs_off[m];
+        B.vals_off = p->vals_off[m];
+        B.row_off = p->row_off[m];
+        p->rhs_off[m + 1] = p->rhs_off[m] + (int64_t)M.L.n * B.k;
+        p->vals_off[m + 1] = p->vals_off[m] + M.L.nnz;
+        p->row_off[m + 1] = p->row_off[m] + M.L.n;
+        // critical path estimate: levels x hop latency vs streamed bytes
+        est[m] = (double)M.nlevels * 150.0 + (double)(M.L.nnz + (int64_t)M.L.n * B.k) * 0.05;
+    }
+    p->have_csc = want_csc;
+    std::vector<int32_t> order((size_t)nmat);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return est[a] > est[b]; });
+    e = p->alloc(&p->d_mats, sizeof(BatchMat) * (size_t)(nmat > 0 ? nmat : 1));
+    if (e == cudaSuccess) e = p->alloc(&p->d_order, sizeof(int32_t) * (size_t)(nmat > 0 ? nmat : 1));
+    if (e == cudaSuccess) e = p->alloc(&p->d_row_off, sizeof(int64_t) * ((size_t)nmat + 1));
+    if (e == cudaSuccess && nmat > 0) e = cudaMemcpy(p->d_mats, hm.data(), sizeof(BatchMat) * nmat, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && nmat > 0) e = cudaMemcpy(p->d_order, order.data(), sizeof(int32_t) * nmat, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(p->d_row_off, p->row_off.data(), sizeof(int64_t) * (nmat + 1), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess || smem > kBlockSmemBudget) { sptrsv_plan_destroy(p); return e != cudaSuccess ? from_cuda(e) : SPTRSV_ENOTSUP; }
+    p->batch_smem = smem;
+    p->batch_grid_sz = std::min(batch_grid(smem, h->di), std::max(nmat, 1));
+    *plan = p;
+    return SPTRSV_OK;
+}
+
+extern "C" sptrsv_status sptrsv_batch_offsets(sptrsv_plan p, int64_t *rhs_offset, int64_t *vals_offset)
+{
+    if (!p || !p->batched) return SPTRSV_EINVAL;
+    if (rhs_offset) std::copy(p->rhs_off.begin(), p->rhs_off.end(), rhs_offset);
+    if (vals_offset) std::copy(p->vals_off.begin(), p->vals_off.end(), vals_offset);
+    return SPTRSV_OK;
+}
+
+namespace {
+sptrsv_status batch_solve_impl(sptrsv_plan p, const void *b, void *x, bool trans)
+{
+    if (!p || !p->batched) return SPTRSV_EINVAL;
+    const int32_t nmat = (int32_t)p->mats.size();
+    if (nmat == 0) return SPTRSV_OK;
+    if (!b || !x) return SPTRSV_EINVAL;
+    if (trans && !p->have_csc) return SPTRSV_ENOTSUP;
+    Waiter w{p->h->d_status, &p->d_ctl->abort_flag, p->spin};
+    cudaError_t e;
+    if (p->dtype == SPTRSV_F64)
+        e = batch_solve<double>(p->d_mats, nmat, p->d_order, (const double *)b, (double *)x, trans, p->d_ctl, w,
+                                p->batch_grid_sz, p->batch_smem, p->h->stream);
+    else
+        e = batch_solve<float>(p->d_mats, nmat, p->d_order, (const float *)b, (float *)x, trans, p->d_ctl, w,
+                               p->batch_grid_sz, p->batch_smem, p->h->stream);
+    return from_cuda(e);
+}
+}  // namespace
+
+extern "C" sptrsv_status sptrsv_batch_solve(sptrsv_plan p, const void *b, void *x)
+{
+    return batch_solve_impl(p, b, x, false);
+}
+
+extern "C" sptrsv_status sptrsv_batch_solve_transpose(sptrsv_plan p, const void *gx, void *gb)
+{
+    return batch_solve_impl(p, gx, gb, true);
+}
+
+extern "C" sptrsv_status sptrsv_batch_grad_vals(sptrsv_plan p, const void *gb, const void *x, void *gvals)
+{
+    if (!p || !p->batched) return SPTRSV_EINVAL;
+    const int32_t nmat = (int32_t)p->mats.size();
+    if (nmat == 0) return SPTRSV_OK;
+    if (!gb || !x || !gvals) return SPTRSV_EINVAL;
+    cudaError_t e;
+    if (p->dtype == SPTRSV_F64)
+        e = batch_grad_vals<double>(p->d_mats, nmat, p->d_row_off, p->row_off[nmat], (const double *)gb,
+                                    (const double *)x, (double *)gvals, p->h->stream);
+    else
+        e = batch_grad_vals<float>(p->d_mats, nmat, p->d_row_off, p->row_off[nmat], (const float *)gb,
+                                   (const float *)x, (float *)gvals, p->h->stream);
+    return from_cuda(e);
+}
+
+extern "C" sptrsv_status sptrsv_batch_tt_apply(sptrsv_plan p, const void *gbp, void *gb)
+{
+    if (!p || !p->batched) return SPTRSV_EINVAL;
+    const int32_t nmat = (int32_t)p->mats.size();
+    if (nmat == 0) return SPTRSV_OK;
+    if (!gbp || !gb) return SPTRSV_EINVAL;
+    cudaError_t e;
+    if (p->dtype == SPTRSV_F64)
+        e = batch_tt_apply<double>(p->d_mats, nmat, p->d_row_off, p->row_off[nmat], p->rhs_off[nmat],
+                                   (const double *)gbp, (double *)gb, p->h->stream);
+    else
+        e = batch_tt_apply<float>(p->d_mats, nmat, p->d_row_off, p->row_off[nmat], p->rhs_off[nmat],
+                                  (const float *)gbp, (float *)gb, p->h->stream);
+    return from_cuda(e);
+}

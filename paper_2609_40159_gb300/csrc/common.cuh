@@ -1,0 +1,121 @@
+// Device-side helpers shared by the sm_103a kernels of the SpTRSV library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "sptrsv.h"
+
+#define SPT_FULL_MASK 0xffffffffu
+
+namespace spt {
+
+// ---------------------------------------------------------------- status word
+// The first error recorded wins; the host reads and clears it.
+__device__ __forceinline__ void set_status(int *status, int code)
+{
+    atomicCAS(status, 0, code);
+}
+
+// -------------------------------------------------- memory-model primitives
+// Ready flags are published with st.release.gpu after the solution values and
+// polled with ld.acquire.gpu before the values are read (PTX memory model:
+// the release/acquire pair orders the value stores before the loads).
+__device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p)
+{
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release(uint32_t *p, uint32_t v)
+{
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ int ld_relaxed(const int *p)
+{
+    int v;
+    asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_relaxed(int *p, int v)
+{
+    asm volatile("st.relaxed.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p)
+{
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void red_release_add(unsigned long long *p, unsigned long long v)
+{
+    asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// Read-only (for the whole kernel) matrix data: non-coherent path.
+template <class T> __device__ __forceinline__ T ldro(const T *p) { return __ldg(p); }
+
+// ------------------------------------------------------------- bounded waits
+// Every spin in this library gives up after `limit` polls: it records
+// SPTRSV_ETIMEOUT, raises the shared abort flag and returns false, so that all
+// other waiters also leave instead of spinning on work that will never come.
+struct Waiter {
+    int *status;
+    int *abort_flag;
+    long long limit;
+};
+
+__device__ __forceinline__ bool aborted(const Waiter &w)
+{
+    return ld_relaxed(w.abort_flag) != 0;
+}
+
+__device__ __forceinline__ void give_up(const Waiter &w)
+{
+    set_status(w.status, SPTRSV_ETIMEOUT);
+    st_relaxed(w.abort_flag, 1);
+}
+
+// Wait until flag == want.  Returns false on timeout / abort.
+__device__ __forceinline__ bool wait_flag(const uint32_t *flag, uint32_t want, const Waiter &w)
+{
+    if (ld_acquire(flag) == want) return true;
+    long long polls = 0;
+    for (;;) {
+        if (ld_acquire(flag) == want) return true;
+        if ((++polls & 255) == 0) {
+            if (aborted(w)) return false;
+            if (polls >= w.limit) { give_up(w); return false; }
+        }
+    }
+}
+
+// Wait until *counter >= target (64-bit monotone progress counter).
+__device__ __forceinline__ bool wait_count(const unsigned long long *counter,
+                                           unsigned long long target, const Waiter &w)
+{
+    if (ld_acquire_u64(counter) >= target) return true;
+    long long polls = 0;
+    for (;;) {
+        if (ld_acquire_u64(counter) >= target) return true;
+        if ((++polls & 255) == 0) {
+            if (aborted(w)) return false;
+            if (polls >= w.limit) { give_up(w); return false; }
+        }
+    }
+}
+
+// ------------------------------------------------------------------ warp ops
+template <class T> __device__ __forceinline__ T shfl_xor(T v, int m)
+{
+    return __shfl_xor_sync(SPT_FULL_MASK, v, m);
+}
+
+__device__ __forceinline__ unsigned lanemask_lt()
+{
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+}  // namespace spt

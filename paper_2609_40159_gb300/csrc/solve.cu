@@ -1,0 +1,574 @@
+// Forward and transpose sparse triangular solves on sm_103a.
+//
+// Kernels (paper Section 2.1 for the level-set method; the related-work
+// section for synchronisation-free solves):
+//   k_level_launch      plain level-set solve: one launch per level, one
+//                       thread per row (the baseline).
+//   k_level_persistent  one launch; warps take row groups in level order from
+//                       a ticket and wait on a grid-wide progress counter
+//                       (rows of all earlier levels done) instead of a launch
+//                       boundary.
+//   k_syncfree          one launch; row groups in row order; each row waits on
+//                       its own predecessors' ready flags (ld.acquire /
+//                       st.release), rows of the same group resolve through
+//                       shared memory.
+//   k_block             one thread block per system; flags and recent
+//                       solutions in a shared-memory ring (for deep, narrow
+//                       systems where the cross-SM round trip dominates).
+// Every kernel handles both L x = b (rows in increasing order) and the
+// adjoint L^T g_b = g_x (rows in decreasing order, reading L through its CSC).
+// A rewritten system L' x = b + T b gathers its T row into the same sum.
+#include "block.cuh"
+
+namespace spt {
+
+// ------------------------------------------------------------ prologue
+__global__ void k_prologue(PlanCtl *ctl)
+{
+    ctl->ticket = 0ull;
+    ctl->progress = 0ull;
+    ctl->epoch = ctl->epoch + 1ull;
+    ctl->abort_flag = 0;
+}
+
+template <class T>
+cudaError_t launch_prologue(PlanCtl *ctl, cudaStream_t s)
+{
+    k_prologue<<<1, 1, 0, s>>>(ctl);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------- plain level set
+template <class T, bool TR>
+__global__ void k_level_launch(Sys<T> A, const int32_t *__restrict__ perm, int32_t q_lo,
+                               int32_t q_hi, Rhs<T> R)
+{
+    const int q = q_lo + blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= q_hi) return;
+    const int i = perm[q];
+    const int a = RV<T, TR>::beg(A, i), e = RV<T, TR>::end(A, i);
+    const T d = RV<T, TR>::diag(A, a, e);
+    const bool ht = !TR && has_trow(A, i);
+    for (int r = 0; r < R.k; ++r) {
+        T s = R.b[(int64_t)i * R.ld + r];
+        if (ht)
+            for (int p = A.trp[i]; p < A.trp[i + 1]; ++p)
+                s += A.tv[p] * R.b[(int64_t)A.tci[p] * R.ld + r];
+        for (int p = a; p < e; ++p)
+            s -= RV<T, TR>::val(A, p) * R.x[(int64_t)RV<T, TR>::col(A, p) * R.ld + r];
+        R.x[(int64_t)i * R.ld + r] = s / d;
+    }
+}
+
+template <class T>
+cudaError_t solve_level_launch(const Sys<T> &A, const int32_t *perm,
+                               const std::vector<int32_t> &h_level_ptr, const Rhs<T> &R,
+                               bool trans, cudaStream_t s)
+{
+    const int L = (int)h_level_ptr.size() - 1;
+    for (int t = 0; t < L; ++t) {
+        const int l = trans ? L - 1 - t : t;
+        const int lo = h_level_ptr[l], hi = h_level_ptr[l + 1];
+        const int blocks = (hi - lo + 255) / 256;
+        if (trans) k_level_launch<T, true><<<blocks, 256, 0, s>>>(A, perm, lo, hi, R);
+        else k_level_launch<T, false><<<blocks, 256, 0, s>>>(A, perm, lo, hi, R);
+    }
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------ shared row computation
+// acc[r] += sum over the row's entries handled by this lane of val * x[col]
+// (all dependencies must already be complete).
+template <class T, int KT, bool TR>
+__device__ __forceinline__ void gather_row(const Sys<T> &A, const Rhs<T> &R, int i, int a, int e,
+                                           int sl, int lpr, int r0, int kt, T (&acc)[KT])
+{
+    if (!TR && has_trow(A, i)) {
+        const int tb = A.trp[i], te = A.trp[i + 1];
+        for (int p = tb + sl; p < te; p += lpr) {
+            const T tv = ldro(A.tv + p);
+            const T *bb = R.b + (int64_t)ldro(A.tci + p) * R.ld + r0;
+#pragma unroll
+            for (int r = 0; r < KT; ++r)
+                if (r < kt) acc[r] -= tv * bb[r];
+        }
+    }
+    for (int p = a + sl; p < e; p += lpr) {
+        const T vv = RV<T, TR>::val(A, p);
+        const T *xx = R.x + (int64_t)RV<T, TR>::col(A, p) * R.ld + r0;
+#pragma unroll
+        for (int r = 0; r < KT; ++r)
+            if (r < kt) acc[r] += vv * xx[r];
+    }
+}
+
+// ------------------------------------------------ persistent level set
+template <class T, int KT, bool TR>
+__global__ void __launch_bounds__(256)
+k_level_persistent(Sys<T> A, Sched S, Rhs<T> R, int rpw, SyncArgs sy)
+{
+    const int lane = threadIdx.x & 31;
+    const int lpr = 32 / rpw;
+    const int g = lane / lpr, sl = lane & (lpr - 1);
+    const int n = A.n, L = S.nlevels;
+    for (;;) {
+        unsigned long long c = 0;
+        if (lane == 0) c = atomicAdd(&sy.ctl->ticket, 1ull);
+        c = __shfl_sync(SPT_FULL_MASK, c, 0);
+        if ((int64_t)c >= S.nchunks) return;
+        const int q0 = (int)c * rpw;
+        const int q1 = min(q0 + rpw, n);
+        int l = S.chunk_level[c];
+        for (;;) {
+            const int lstart = TR ? n - S.level_ptr[L - l] : S.level_ptr[l];
+            const int lend = TR ? n - S.level_ptr[L - 1 - l] : S.level_ptr[l + 1];
+            const int lo = max(q0, lstart), hi = min(q1, lend);
+            int ok = 1;
+            if (lane == 0) ok = wait_count(&sy.ctl->progress, (unsigned long long)lstart, sy.w);
+            ok = __shfl_sync(SPT_FULL_MASK, ok, 0);
+            if (!ok) return;
+            __syncwarp();
+            const int q = q0 + g;
+            const bool active = q >= lo && q < hi;
+            const int i = active ? (TR ? S.perm[n - 1 - q] : S.perm[q]) : 0;
+            const int a = active ? RV<T, TR>::beg(A, i) : 0;
+            const int e = active ? RV<T, TR>::end(A, i) : 0;
+            for (int r0 = 0; r0 < R.k; r0 += KT) {
+                const int kt = min(KT, R.k - r0);
+                T acc[KT];
+#pragma unroll
+                for (int r = 0; r < KT; ++r) acc[r] = T(0);
+                if (active) gather_row<T, KT, TR>(A, R, i, a, e, sl, lpr, r0, kt, acc);
+                group_reduce<T, KT>(acc, lpr);
+                if (active && sl == 0) {
+                    const T d = RV<T, TR>::diag(A, a, e);
+                    const T *bb = R.b + (int64_t)i * R.ld + r0;
+                    T *xx = R.x + (int64_t)i * R.ld + r0;
+#pragma unroll
+                    for (int r = 0; r < KT; ++r)
+                        if (r < kt) xx[r] = (bb[r] - acc[r]) / d;
+                }
+            }
+            __syncwarp();
+            if (lane == 0) {
+                __threadfence();
+                atomicAdd(&sy.ctl->progress, (unsigned long long)(hi - lo));
+            }
+            if (hi >= q1) break;
+            ++l;
+        }
+    }
+}
+
+// --------------------------------------------------------- sync-free
+constexpr int kSfThreads = 256;
+constexpr int kSfWarps = kSfThreads / 32;
+
+template <class T, int KT, bool TR>
+__global__ void __launch_bounds__(kSfThreads)
+k_syncfree(Sys<T> A, Rhs<T> R, int rpw, SyncArgs sy)
+{
+    __shared__ T xs_all[kSfWarps][32 * KT];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    volatile T *xs = xs_all[wid];
+    const int lpr = 32 / rpw;
+    const int g = lane / lpr, sl = lane & (lpr - 1);
+    const unsigned gm = lpr == 32 ? 0xffffffffu : ((1u << lpr) - 1u);
+    const int n = A.n;
+    const uint32_t epoch = (uint32_t)sy.ctl->epoch;
+    const int64_t nchunks = ((int64_t)n + rpw - 1) / rpw;
+    for (;;) {
+        unsigned long long c = 0;
+        if (lane == 0) c = atomicAdd(&sy.ctl->ticket, 1ull);
+        c = __shfl_sync(SPT_FULL_MASK, c, 0);
+        if ((int64_t)c >= nchunks) return;
+        const int base = (int)c * rpw;
+        const int pos = base + g;
+        const bool valid = pos < n;
+        const int i = valid ? (TR ? n - 1 - pos : pos) : 0;
+        const int a = valid ? RV<T, TR>::beg(A, i) : 0;
+        const int e = valid ? RV<T, TR>::end(A, i) : 0;
+        const unsigned leaders = __ballot_sync(SPT_FULL_MASK, valid && sl == 0);
+        for (int r0 = 0; r0 < R.k; r0 += KT) {
+            const int kt = min(KT, R.k - r0);
+            const bool last_tile = r0 + KT >= R.k;
+            T acc[KT];
+#pragma unroll
+            for (int r = 0; r < KT; ++r) acc[r] = T(0);
+            if (!TR && valid && has_trow(A, i)) {
+                const int tb = A.trp[i], te = A.trp[i + 1];
+                for (int p = tb + sl; p < te; p += lpr) {
+                    const T tv = ldro(A.tv + p);
+                    const T *bb = R.b + (int64_t)ldro(A.tci + p) * R.ld + r0;
+#pragma unroll
+                    for (int r = 0; r < KT; ++r)
+                        if (r < kt) acc[r] -= tv * bb[r];
+                }
+            }
+            int p = a + sl;
+            unsigned fin = 0;
+            bool failed = false;
+            for (;;) {
+                const bool open = valid && !((fin >> (g * lpr)) & 1u);
+                if (open) {
+                    while (p < e) {
+                        const int j = RV<T, TR>::col(A, p);
+                        const int pj = order_pos<TR>(n, j);
+                        const T vv = RV<T, TR>::val(A, p);
+                        if (pj >= base) {
+                            const int gj = pj - base;
+                            if (!((fin >> (gj * lpr)) & 1u)) break;
+#pragma unroll
+                            for (int r = 0; r < KT; ++r)
+                                if (r < kt) acc[r] += vv * xs[gj * KT + r];
+                        } else {
+                            if (!wait_flag(sy.flags + j, epoch, sy.w)) { failed = true; break; }
+                            const T *xx = R.x + (int64_t)j * R.ld + r0;
+#pragma unroll
+                            for (int r = 0; r < KT; ++r)
+                                if (r < kt) acc[r] += vv * xx[r];
+                        }
+                        p += lpr;
+                    }
+                }
+                const bool ready = !open || p >= e || failed;
+                const unsigned bal = __ballot_sync(SPT_FULL_MASK, ready);
+                if (__any_sync(SPT_FULL_MASK, failed)) return;
+                const bool grp_ready = ((bal >> (g * lpr)) & gm) == gm;
+                const bool newly = open && grp_ready;
+                if (__any_sync(SPT_FULL_MASK, newly)) {
+                    T red[KT];
+#pragma unroll
+                    for (int r = 0; r < KT; ++r) red[r] = acc[r];
+                    group_reduce<T, KT>(red, lpr);
+                    if (newly && sl == 0) {
+                        const T d = RV<T, TR>::diag(A, a, e);
+                        const T *bb = R.b + (int64_t)i * R.ld + r0;
+                        T *xx = R.x + (int64_t)i * R.ld + r0;
+#pragma unroll
+                        for (int r = 0; r < KT; ++r)
+                            if (r < kt) {
+                                const T xv = (bb[r] - red[r]) / d;
+                                xs[g * KT + r] = xv;
+                                xx[r] = xv;
+                            }
+                        if (last_tile && i != sy.withhold) st_release(sy.flags + i, epoch);
+                    }
+                }
+                fin |= __ballot_sync(SPT_FULL_MASK, newly && sl == 0);
+                __syncwarp();
+                if ((fin & leaders) == leaders) break;
+            }
+        }
+    }
+}
+
+constexpr int kBlockThreads = 512;
+
+template <class T, int KT, bool TR>
+__global__ void __launch_bounds__(kBlockThreads)
+k_block(Sys<T> A, Rhs<T> R, int rpw, int kc, int P, SyncArgs sy)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int ring = kc * rpw;
+    BlockSmem<T, KT> sm = carve_block_smem<T, KT>(smraw, ring, kc);
+    reset_block_smem<T, KT>(sm, ring, kc);
+    __syncthreads();
+    block_solve<T, KT, TR>(A, R, rpw, kc, P, sm, sy.w, sy.withhold);
+}
+
+size_t block_smem_bytes(int rpw, int kt, int kc, bool f64)
+{
+    const size_t ring = (size_t)kc * rpw;
+    return ring * kt * (f64 ? 8 : 4) + ring * 4 + (size_t)kc * 4 + 16;
+}
+
+// ------------------------------------------------------------- gradient
+template <class T>
+__global__ void k_grad_vals(Sys<T> A, const T *__restrict__ gb, const T *__restrict__ x,
+                            int64_t ld, int32_t k, T *__restrict__ gv)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    // 4 rows per warp, 8 lanes per row
+    const int g = lane >> 3, sl = lane & 7;
+    for (int64_t r4 = gw * 4; r4 < A.n; r4 += nw * 4) {
+        const int64_t i = r4 + g;
+        if (i >= A.n) continue;
+        const int a = ldro(A.rp + i), e = ldro(A.rp + i + 1);
+        const T *gi = gb + i * ld;
+        for (int p = a + sl; p < e; p += 8) {
+            const T *xj = x + (int64_t)ldro(A.ci + p) * ld;
+            T s = T(0);
+            for (int r = 0; r < k; ++r) s += gi[r] * xj[r];
+            gv[p] = -s;
+        }
+    }
+}
+
+template <class T>
+cudaError_t grad_vals(const Sys<T> &A, const T *gb, const T *x, int64_t ld, int32_t k, T *gv,
+                      cudaStream_t s)
+{
+    if (A.n <= 0) return cudaSuccess;
+    int64_t blocks = ((int64_t)A.n + 31) / 32;
+    if (blocks > 65535 * 4) blocks = 65535 * 4;
+    k_grad_vals<T><<<(int)blocks, 256, 0, s>>>(A, gb, x, ld, k, gv);
+    return cudaGetLastError();
+}
+
+// -------------------------------------------------------------- T^T apply
+template <class T>
+__global__ void k_copy_rhs(const T *src, T *dst, int64_t n, int64_t ld, int32_t k)
+{
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n * k;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = t / k, r = t - i * k;
+        dst[i * ld + r] = src[i * ld + r];
+    }
+}
+
+template <class T>
+__global__ void k_tt_scatter(Sys<T> A, const T *__restrict__ gbp, T *gb, int64_t ld, int32_t k)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = gw; i < A.n; i += nw) {
+        if (!has_trow(A, (int)i)) continue;
+        const int a = A.trp[i], e = A.trp[i + 1];
+        for (int p = a + lane; p < e; p += 32) {
+            const T tv = A.tv[p];
+            const int64_t j = A.tci[p];
+            for (int r = 0; r < k; ++r) atomicAdd(gb + j * ld + r, tv * gbp[i * ld + r]);
+        }
+    }
+}
+
+template <class T>
+cudaError_t tt_apply(const Sys<T> &A, const T *gbp, T *gb, int64_t ld, int32_t k, cudaStream_t s)
+{
+    if (A.n <= 0) return cudaSuccess;
+    int64_t blocks = ((int64_t)A.n * k + 255) / 256;
+    if (blocks > 65535 * 4) blocks = 65535 * 4;
+    k_copy_rhs<T><<<(int)blocks, 256, 0, s>>>(gbp, gb, A.n, ld, k);
+    if (A.tmask) {
+        int64_t wb = ((int64_t)A.n + 7) / 8;
+        if (wb > 65535 * 4) wb = 65535 * 4;
+        k_tt_scatter<T><<<(int)wb, 256, 0, s>>>(A, gbp, gb, ld, k);
+    }
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------ plan helpers
+__global__ void k_build_tmask(const int32_t *trp, int32_t n, uint32_t *tmask)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ((int64_t)n + 31) / 32 * 32;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const bool has = i < n && trp[i + 1] > trp[i];
+        const unsigned m = __ballot_sync(SPT_FULL_MASK, has);
+        if ((threadIdx.x & 31) == 0) tmask[i >> 5] = m;
+    }
+}
+
+cudaError_t build_tmask(const int32_t *trp, int32_t n, uint32_t *tmask, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    int64_t blocks = (((int64_t)n + 31) / 32 * 32 + 255) / 256;
+    if (blocks > 65535) blocks = 65535;  // grid-stride keeps whole warps together
+    k_build_tmask<<<(int)blocks, 256, 0, s>>>(trp, n, tmask);
+    return cudaGetLastError();
+}
+
+__global__ void k_chunk_levels(const int32_t *level_ptr, int32_t L, int32_t n, int rpw, bool trans,
+                               int32_t *chunk_level, int64_t nchunks)
+{
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < nchunks;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        const int q0 = (int)(c * rpw);
+        const int q = trans ? n - 1 - q0 : q0;  // original perm position
+        // largest l with level_ptr[l] <= q
+        int lo = 0, hi = L - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (level_ptr[mid] <= q) lo = mid; else hi = mid - 1;
+        }
+        chunk_level[c] = trans ? L - 1 - lo : lo;
+    }
+}
+
+cudaError_t build_chunk_levels(const int32_t *level_ptr, int32_t nlevels, int32_t n, int rpw,
+                               bool trans, int32_t *chunk_level, cudaStream_t s)
+{
+    const int64_t nchunks = ((int64_t)n + rpw - 1) / rpw;
+    if (nchunks <= 0) return cudaSuccess;
+    int64_t blocks = (nchunks + 255) / 256;
+    if (blocks > 65535) blocks = 65535;
+    k_chunk_levels<<<(int)blocks, 256, 0, s>>>(level_ptr, nlevels, n, rpw, trans, chunk_level, nchunks);
+    return cudaGetLastError();
+}
+
+// --------------------------------------------------------- dispatchers
+template <class T, int KT>
+static cudaError_t lp_launch(const Sys<T> &A, const Sched &S, const Rhs<T> &R, int rpw, bool trans,
+                             const SyncArgs &sy, int grid, cudaStream_t s)
+{
+    if (trans) k_level_persistent<T, KT, true><<<grid, 256, 0, s>>>(A, S, R, rpw, sy);
+    else k_level_persistent<T, KT, false><<<grid, 256, 0, s>>>(A, S, R, rpw, sy);
+    return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t solve_level_persistent(const Sys<T> &A, const Sched &S, const Rhs<T> &R, int rpw,
+                                   int kt, bool trans, const SyncArgs &sy, int grid, cudaStream_t s)
+{
+    cudaError_t e = launch_prologue<T>(sy.ctl, s);
+    if (e != cudaSuccess || A.n <= 0) return e;
+    switch (kt) {
+    case 1: return lp_launch<T, 1>(A, S, R, rpw, trans, sy, grid, s);
+    case 2: return lp_launch<T, 2>(A, S, R, rpw, trans, sy, grid, s);
+    case 4: return lp_launch<T, 4>(A, S, R, rpw, trans, sy, grid, s);
+    case 8: return lp_launch<T, 8>(A, S, R, rpw, trans, sy, grid, s);
+    default: return lp_launch<T, 16>(A, S, R, rpw, trans, sy, grid, s);
+    }
+}
+
+template <class T, int KT>
+static cudaError_t sf_launch(const Sys<T> &A, const Rhs<T> &R, int rpw, bool trans,
+                             const SyncArgs &sy, int grid, cudaStream_t s)
+{
+    if (trans) k_syncfree<T, KT, true><<<grid, kSfThreads, 0, s>>>(A, R, rpw, sy);
+    else k_syncfree<T, KT, false><<<grid, kSfThreads, 0, s>>>(A, R, rpw, sy);
+    return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t solve_syncfree(const Sys<T> &A, const Rhs<T> &R, int rpw, int kt, bool trans,
+                           const SyncArgs &sy, int grid, cudaStream_t s)
+{
+    cudaError_t e = launch_prologue<T>(sy.ctl, s);
+    if (e != cudaSuccess || A.n <= 0) return e;
+    switch (kt) {
+    case 1: return sf_launch<T, 1>(A, R, rpw, trans, sy, grid, s);
+    case 2: return sf_launch<T, 2>(A, R, rpw, trans, sy, grid, s);
+    case 4: return sf_launch<T, 4>(A, R, rpw, trans, sy, grid, s);
+    case 8: return sf_launch<T, 8>(A, R, rpw, trans, sy, grid, s);
+    default: return sf_launch<T, 16>(A, R, rpw, trans, sy, grid, s);
+    }
+}
+
+
+void block_geometry(int rpw, int kt, bool f64, int *kc, int *P)
+{
+    const int warps = kBlockThreads / 32;
+    *P = warps + 2;
+    *kc = 2 * (*P);
+    while (*kc < 4096 / rpw && block_smem_bytes(rpw, kt, (*kc) * 2, f64) <= kBlockSmemBudget / 2)
+        *kc *= 2;  // a longer ring keeps more dependencies in shared memory
+}
+
+// The dynamic shared-memory limit is raised once per kernel instantiation
+// (outside any stream capture: plans run a first solve before capturing).
+template <class K> static void raise_smem_once(K kernel)
+{
+    static bool done = false;
+    if (!done) {
+        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBlockSmemBudget);
+        done = true;
+    }
+}
+
+template <class T, int KT>
+static cudaError_t blk_launch(const Sys<T> &A, const Rhs<T> &R, int rpw, bool trans,
+                              const SyncArgs &sy, cudaStream_t s)
+{
+    int kc, P;
+    block_geometry(rpw, KT, sizeof(T) == 8, &kc, &P);
+    const size_t smem = block_smem_bytes(rpw, KT, kc, sizeof(T) == 8);
+    if (smem > kBlockSmemBudget) return cudaErrorInvalidConfiguration;
+    if (trans) {
+        raise_smem_once(k_block<T, KT, true>);
+        k_block<T, KT, true><<<1, kBlockThreads, smem, s>>>(A, R, rpw, kc, P, sy);
+    } else {
+        raise_smem_once(k_block<T, KT, false>);
+        k_block<T, KT, false><<<1, kBlockThreads, smem, s>>>(A, R, rpw, kc, P, sy);
+    }
+    return cudaGetLastError();
+}
+
+int block_kt_for(int k)
+{
+    int kt = 1;
+    while (kt < k) kt <<= 1;
+    return kt;
+}
+
+bool block_mode_supported(int k, bool f64)
+{
+    if (k < 1 || k > 32) return false;
+    const int kt = block_kt_for(k);
+    int kc, P;
+    block_geometry(1, kt, f64, &kc, &P);
+    if (block_smem_bytes(1, kt, kc, f64) > kBlockSmemBudget) return false;
+    block_geometry(32, kt, f64, &kc, &P);
+    return block_smem_bytes(32, kt, kc, f64) <= kBlockSmemBudget;
+}
+
+template <class T>
+cudaError_t solve_block(const Sys<T> &A, const Rhs<T> &R, int rpw, int kt, bool trans,
+                        const SyncArgs &sy, cudaStream_t s)
+{
+    (void)kt;
+    cudaError_t e = launch_prologue<T>(sy.ctl, s);
+    if (e != cudaSuccess || A.n <= 0) return e;
+    switch (block_kt_for(R.k)) {
+    case 1: return blk_launch<T, 1>(A, R, rpw, trans, sy, s);
+    case 2: return blk_launch<T, 2>(A, R, rpw, trans, sy, s);
+    case 4: return blk_launch<T, 4>(A, R, rpw, trans, sy, s);
+    case 8: return blk_launch<T, 8>(A, R, rpw, trans, sy, s);
+    case 16: return blk_launch<T, 16>(A, R, rpw, trans, sy, s);
+    default: return blk_launch<T, 32>(A, R, rpw, trans, sy, s);
+    }
+}
+
+int persistent_grid_level(int kt, bool f64, const DeviceInfo &di)
+{
+    int per_sm = 0;
+    if (f64) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_level_persistent<double, 1, false>, 256, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_level_persistent<float, 1, false>, 256, 0);
+    (void)kt;
+    if (per_sm < 1) per_sm = 1;
+    return per_sm * di.num_sms;
+}
+
+int persistent_grid_syncfree(int kt, bool f64, const DeviceInfo &di)
+{
+    int per_sm = 0;
+    if (f64) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_syncfree<double, 1, false>, kSfThreads, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_syncfree<float, 1, false>, kSfThreads, 0);
+    (void)kt;
+    if (per_sm < 1) per_sm = 1;
+    return per_sm * di.num_sms;
+}
+
+// ------------------------------------------------ explicit instantiations
+#define SPT_INST(T)                                                                                     \
+    template cudaError_t launch_prologue<T>(PlanCtl *, cudaStream_t);                                   \
+    template cudaError_t solve_level_launch<T>(const Sys<T> &, const int32_t *,                         \
+                                               const std::vector<int32_t> &, const Rhs<T> &, bool,     \
+                                               cudaStream_t);                                           \
+    template cudaError_t solve_level_persistent<T>(const Sys<T> &, const Sched &, const Rhs<T> &, int, \
+                                                   int, bool, const SyncArgs &, int, cudaStream_t);     \
+    template cudaError_t solve_syncfree<T>(const Sys<T> &, const Rhs<T> &, int, int, bool,              \
+                                           const SyncArgs &, int, cudaStream_t);                        \
+    template cudaError_t solve_block<T>(const Sys<T> &, const Rhs<T> &, int, int, bool,                 \
+                                        const SyncArgs &, cudaStream_t);                                \
+    template cudaError_t grad_vals<T>(const Sys<T> &, const T *, const T *, int64_t, int32_t, T *,      \
+                                      cudaStream_t);                                                    \
+    template cudaError_t tt_apply<T>(const Sys<T> &, const T *, T *, int64_t, int32_t, cudaStream_t);
+SPT_INST(double)
+SPT_INST(float)
+#undef SPT_INST
+
+}  // namespace spt

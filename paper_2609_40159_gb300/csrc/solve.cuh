@@ -1,0 +1,142 @@
+// Solve-side data views and launchers (forward solve, transpose solve,
+// value gradient, T application) shared by solve.cu, batch.cu and api.cu.
+#pragma once
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace spt {
+
+// A lower-triangular system as the kernels see it.
+template <class T> struct Sys {
+    int32_t n;
+    const int32_t *rp;    // CSR of L
+    const int32_t *ci;
+    const T *v;
+    const int32_t *cp;    // CSC of L (transpose solve): column pointers,
+    const int32_t *crow;  //   row of every CSC entry (diagonal first),
+    const int32_t *tmap;  //   CSR position of every CSC entry
+    const int32_t *trp;   // T of a rewritten system (rows with entries only)
+    const int32_t *tci;
+    const T *tv;
+    const uint32_t *tmask;  // bit i set when row i has a T row; null = no T
+};
+
+// Level schedule.
+struct Sched {
+    const int32_t *perm;
+    const int32_t *level_ptr;
+    int32_t nlevels;
+    const int32_t *chunk_level;  // level of the first row of every row group
+    int64_t nchunks;
+};
+
+template <class T> struct Rhs {
+    const T *b;
+    T *x;
+    int64_t ld;
+    int32_t k;
+};
+
+// Per-plan device control block.
+struct PlanCtl {
+    unsigned long long ticket;
+    unsigned long long progress;
+    unsigned long long epoch;
+    unsigned long long spare;
+    int abort_flag;
+    int pad[3];
+};
+
+struct SyncArgs {
+    uint32_t *flags;
+    PlanCtl *ctl;
+    int32_t withhold;
+    Waiter w;
+};
+
+// ---------------------------------------------------------------- launchers
+// All return cudaSuccess or the launch error; T = double or float.
+template <class T>
+cudaError_t launch_prologue(PlanCtl *ctl, cudaStream_t s);
+
+template <class T>
+cudaError_t solve_level_launch(const Sys<T> &A, const int32_t *perm,
+                               const std::vector<int32_t> &h_level_ptr, const Rhs<T> &R,
+                               bool trans, cudaStream_t s);
+
+template <class T>
+cudaError_t solve_level_persistent(const Sys<T> &A, const Sched &S, const Rhs<T> &R, int rpw,
+                                   int kt, bool trans, const SyncArgs &sy, int grid,
+                                   cudaStream_t s);
+
+template <class T>
+cudaError_t solve_syncfree(const Sys<T> &A, const Rhs<T> &R, int rpw, int kt, bool trans,
+                           const SyncArgs &sy, int grid, cudaStream_t s);
+
+template <class T>
+cudaError_t solve_block(const Sys<T> &A, const Rhs<T> &R, int rpw, int kt, bool trans,
+                        const SyncArgs &sy, cudaStream_t s);
+
+template <class T>
+cudaError_t grad_vals(const Sys<T> &A, const T *gb, const T *x, int64_t ld, int32_t k, T *gv,
+                      cudaStream_t s);
+
+template <class T>
+cudaError_t tt_apply(const Sys<T> &A, const T *gbp, T *gb, int64_t ld, int32_t k,
+                     cudaStream_t s);
+
+cudaError_t build_tmask(const int32_t *trp, int32_t n, uint32_t *tmask, cudaStream_t s);
+cudaError_t build_chunk_levels(const int32_t *level_ptr, int32_t nlevels, int32_t n, int rpw,
+                               bool trans, int32_t *chunk_level, cudaStream_t s);
+
+// Occupancy-derived persistent grid sizes.
+int persistent_grid_level(int kt, bool f64, const DeviceInfo &di);
+int persistent_grid_syncfree(int kt, bool f64, const DeviceInfo &di);
+// Block mode: whether (k, dtype) fits the shared-memory ring.
+bool block_mode_supported(int k, bool f64);
+int block_kt_for(int k);
+// Ring geometry of the block mode: kc row groups in the ring, throttle P.
+void block_geometry(int rpw, int kt, bool f64, int *kc, int *P);
+size_t block_smem_bytes(int rpw, int kt, int kc, bool f64);
+constexpr size_t kBlockSmemBudget = 200 * 1024;
+
+// ---------------------------------------------------------------- batched
+// Per-matrix descriptor of a batched plan (device resident).
+struct BatchMat {
+    int32_t n;
+    int32_t k;        // right-hand sides
+    int32_t rpw;      // rows per warp
+    int32_t kt;       // rhs register tile (>= k)
+    int32_t kc;       // ring row groups (block mode)
+    int32_t P;        // throttle distance in row groups
+    int64_t nnz;
+    const int32_t *rp, *ci;
+    const void *v;
+    const int32_t *cp, *crow, *tmap;
+    const int32_t *trp, *tci;
+    const void *tv;
+    const uint32_t *tmask;
+    int64_t rhs_off;   // element offset of the [n x k] block in packed buffers
+    int64_t vals_off;  // element offset of the nnz values in packed gradients
+    int64_t row_off;   // first global row of the matrix
+};
+
+// One persistent launch: thread blocks take matrices in `order` from the
+// control block's ticket and solve each with the block algorithm.
+template <class T>
+cudaError_t batch_solve(const BatchMat *mats, int32_t nmat, const int32_t *order, const T *b,
+                        T *x, bool trans, PlanCtl *ctl, const Waiter &w, int grid,
+                        size_t smem, cudaStream_t s);
+// Value gradients of all matrices (row_off: nmat+1 prefix of n, device).
+template <class T>
+cudaError_t batch_grad_vals(const BatchMat *mats, int32_t nmat, const int64_t *row_off,
+                            int64_t total_rows, const T *gb, const T *x, T *gv, cudaStream_t s);
+// gb = gbp + T^T gbp for every rewritten matrix (packed buffers).
+template <class T>
+cudaError_t batch_tt_apply(const BatchMat *mats, int32_t nmat, const int64_t *row_off,
+                           int64_t total_rows, int64_t total_rhs, const T *gbp, T *gb,
+                           cudaStream_t s);
+int batch_grid(size_t smem, const DeviceInfo &di);
+
+}  // namespace spt

@@ -1,0 +1,61 @@
+"""The C ABI boundary without a GPU: the in-tree library builds, loads, and
+exports exactly the entry points that include/sptrsv.h declares; the Python
+binding declares the same names.  No compute call is made."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "sptrsv.h")
+
+
+def _declared():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(sptrsv_[a-z_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib_path():
+    from paper_2609_40159_gb300 import build
+    return build.build()
+
+
+def test_library_exports_every_declared_symbol(lib_path):
+    out = subprocess.run(["nm", "-D", "--defined-only", lib_path], capture_output=True, text=True,
+                         check=True).stdout
+    exported = sorted({ln.split()[-1] for ln in out.splitlines() if ln.split()[-1].startswith("sptrsv_")})
+    assert exported == _declared()
+
+
+def test_binding_declares_same_names(lib_path):
+    from paper_2609_40159_gb300 import _lib
+    assert _lib.DECLARED == _declared()
+    lib = _lib.load(lib_path)
+    for name in _declared():
+        assert hasattr(lib, name)
+    assert lib.sptrsv_status_string(7) == b"a bounded device wait gave up"
+    assert lib.sptrsv_status_string(0) == b"ok"
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    from paper_2609_40159_gb300 import _lib
+    with pytest.raises(OSError, match="no CPU fallback"):
+        _lib.load(str(tmp_path / "missing.so"))
+
+
+def test_header_compiles_as_plain_c(tmp_path):
+    c = tmp_path / "use.c"
+    c.write_text('#include "sptrsv.h"\nint main(void){ sptrsv_plan_opts o = {0}; return (int)o.mode; }\n')
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"),
+                    "-c", str(c), "-o", str(tmp_path / "use.o")], check=True)
+
+
+def test_status_codes_match_header():
+    from paper_2609_40159_gb300 import _lib
+    src = open(HEADER).read()
+    for name, val in re.findall(r"(SPTRSV_E[A-Z]+|SPTRSV_OK)\s*=\s*(\d+)", src):
+        assert getattr(_lib, name) == int(val)

@@ -1,0 +1,89 @@
+"""Level analysis and validation on the GPU vs the CPU oracle: levels, the
+level partition, costs and the statistics must match bit for bit."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synthetic as S
+from helpers import cases_small
+
+pytestmark = pytest.mark.gpu
+
+
+def _check(A_h):
+    import paper_2609_40159_gb300 as P
+    A = P.Matrix.from_host(A_h)
+    an = P.analyze(A)
+    ref = oracle.analyze(A_h)
+    assert an.nlevels == ref["nlevels"]
+    assert np.array_equal(an.lev.cpu().numpy(), ref["lev"])
+    assert np.array_equal(an.perm.cpu().numpy(), ref["perm"])
+    assert np.array_equal(an.level_ptr.cpu().numpy(), ref["level_ptr"])
+    assert np.array_equal(an.cost.cpu().numpy(), ref["cost"])
+    assert np.array_equal(an.stats, ref["stats"]), (an.stats, ref["stats"])  # bit-exact
+    return an
+
+
+@pytest.mark.parametrize("name,A", cases_small(), ids=[c[0] for c in cases_small()])
+def test_analyze_small(name, A):
+    _check(A)
+
+
+def test_analyze_fp32_same_as_fp64():
+    _check(S.band_random(5000, 100, 4, 16, seed=9).astype(np.float32))
+
+
+@pytest.mark.parametrize("gen", ["lap2d_1024", "lap3d_128", "powerlaw_4M"])
+def test_analyze_full_size(gen):
+    A = {"lap2d_1024": lambda: S.lap2d(1024), "lap3d_128": lambda: S.lap3d(128),
+         "powerlaw_4M": lambda: S.powerlaw(4_000_000, alpha=2.1, seed=2)}[gen]()
+    an = _check(A)
+    if gen == "lap2d_1024":
+        assert an.nlevels == 2047
+    if gen == "lap3d_128":
+        assert an.nlevels == 382
+
+
+def test_analyze_deterministic():
+    import paper_2609_40159_gb300 as P
+    A = P.Matrix.from_host(S.powerlaw(300_000, seed=4))
+    a1, a2 = P.analyze(A), P.analyze(A)
+    for f in ("lev", "perm", "level_ptr", "cost"):
+        assert torch.equal(getattr(a1, f), getattr(a2, f))
+    assert np.array_equal(a1.stats, a2.stats)
+
+
+def test_empty_matrix():
+    import paper_2609_40159_gb300 as P
+    A = P.Matrix(torch.zeros(1, dtype=torch.int32, device="cuda"),
+                 torch.zeros(0, dtype=torch.int32, device="cuda"),
+                 torch.zeros(0, dtype=torch.float64, device="cuda"))
+    an = P.analyze(A)
+    assert an.nlevels == 0 and np.all(an.stats == 0)
+
+
+def _broken(kind):
+    A = S.band_random(300, 10, 1, 4, seed=1)
+    rp, ci, v = A.row_ptr.copy(), A.col_idx.copy(), A.vals.copy()
+    if kind == "zero_diag":
+        v[rp[41] - 1] = 0.0
+    elif kind == "upper":
+        ci[rp[77]] = 200
+    elif kind == "unsorted":
+        a = rp[150]
+        ci[a], ci[a + 1] = ci[a + 1], ci[a]
+    elif kind == "no_diag":
+        ci[rp[201] - 1] = 199
+    return S.CSR(A.n, rp, ci, v)
+
+
+@pytest.mark.parametrize("kind", ["zero_diag", "upper", "unsorted", "no_diag"])
+def test_validate_codes_match_oracle(kind):
+    import paper_2609_40159_gb300 as P
+    A_h = _broken(kind)
+    st, row = P.validate(P.Matrix.from_host(A_h))
+    assert (st, row) == oracle.validate(A_h)
+    assert st != 0
+    with pytest.raises(P._lib.SpTRSVError):
+        P.analyze(P.Matrix.from_host(A_h))

@@ -1,0 +1,232 @@
+"""Forward and transpose solves, value gradients and the autograd Function on
+the GPU vs the CPU oracle.  x is judged by normwise relative error: 1e-12 for
+FP64, 1e-5 for FP32 values with FP32 accumulation (against the FP64 solution
+of the system the FP32 values define)."""
+import functools
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synthetic as S
+from helpers import TOL, cases_small, relerr, widened
+
+pytestmark = pytest.mark.gpu
+
+MODES = ["level_launch", "level", "syncfree", "block"]
+RPWS = [1, 4, 32]
+KS = [1, 3, 32]
+
+
+@functools.lru_cache(maxsize=None)
+def _case(name):
+    return dict(cases_small())[name]
+
+
+@functools.lru_cache(maxsize=None)
+def _ref(name, k, dt):
+    A_h = _case(name).astype(dt)
+    b = S.rhs(A_h.n, k, seed=k, dtype=dt)
+    return A_h, b, oracle.solve(widened(A_h), b), oracle.solve_transpose(widened(A_h), b)
+
+
+NAMES = [c[0] for c in cases_small()]
+
+
+@pytest.mark.parametrize("dt", [np.float64, np.float32], ids=["f64", "f32"])
+@pytest.mark.parametrize("name", NAMES)
+def test_solve_all_modes(name, dt):
+    import paper_2609_40159_gb300 as P
+    for k in KS:
+        A_h, b_h, x_ref, g_ref = _ref(name, k, dt)
+        A = P.Matrix.from_host(A_h)
+        b = torch.as_tensor(b_h).cuda()
+        plan = P.Plan(A, transpose=True)
+        for mode in MODES:
+            for rpw in RPWS:
+                for kt in (1, 4, 16):
+                    if mode == "level_launch" and (rpw, kt) != (32, 16):
+                        continue
+                    plan.set(mode, rpw, kt)
+                    x = plan.solve(b)
+                    e = relerr(x.cpu().numpy(), x_ref)
+                    assert e <= TOL[dt], (mode, rpw, kt, k, e)
+                    g = plan.solve_transpose(b)
+                    e = relerr(g.cpu().numpy(), g_ref)
+                    assert e <= TOL[dt], ("T", mode, rpw, kt, k, e)
+        assert P.handle().status() == 0
+
+
+@pytest.mark.parametrize("name", ["cfg0", "lap2d_97", "powerlaw", "long_row"])
+def test_grad_vals(name):
+    import paper_2609_40159_gb300 as P
+    A_h = _case(name)
+    b_h = S.rhs(A_h.n, 4, seed=1)
+    w_h = S.rhs(A_h.n, 4, seed=2)
+    A = P.Matrix.from_host(A_h)
+    plan = P.Plan(A, transpose=True)
+    x = plan.solve(torch.as_tensor(b_h).cuda())
+    gb = plan.solve_transpose(torch.as_tensor(w_h).cuda())
+    gv = plan.grad_vals(gb, x).cpu().numpy()
+    ref = oracle.grad_vals(A_h, oracle.solve_transpose(A_h, w_h), oracle.solve(A_h, b_h))
+    assert relerr(gv, ref) <= 1e-12
+
+
+def test_rewritten_solve_and_adjoint_identity():
+    import paper_2609_40159_gb300 as P
+    A_h = S.band_random(20_000, 200, 4, 16, seed=3)
+    an = oracle.analyze(A_h)
+    rows, tg = S.narrowest_levels_list(an["nlevels"], an["level_ptr"], an["perm"], 0.02, 8)
+    A = P.Matrix.from_host(A_h)
+    Lp, T = P.rewrite(A, P.analyze(A).lev, rows, tg)
+    b_h = S.rhs(A_h.n, 3, seed=5)
+    b = torch.as_tensor(b_h).cuda()
+    x_ref = oracle.solve(A_h, b_h)
+    plan = P.Plan(Lp, T, transpose=True)
+    orig = P.Plan(A, transpose=True)
+    for mode in MODES:
+        plan.set(mode, 32, 4)
+        assert relerr(plan.solve(b).cpu().numpy(), x_ref) <= 1e-12, mode
+        gbp = plan.solve_transpose(b)
+        gb = plan.tt_apply(gbp).cpu().numpy()
+        assert relerr(gb, orig.solve_transpose(b).cpu().numpy()) <= 1e-12, mode
+        assert relerr(gb, oracle.solve_transpose(A_h, b_h)) <= 1e-12
+
+
+def test_autograd_finite_differences_lap3d_block():
+    import paper_2609_40159_gb300 as P
+    A_h = S.leading_block(S.lap3d(128), 4096)
+    A = P.Matrix.from_host(A_h)
+    plan = P.Plan(A, transpose=True)
+    b = torch.as_tensor(S.rhs(A_h.n, 8, seed=4)).cuda().requires_grad_(True)
+    w = torch.as_tensor(S.rhs(A_h.n, 8, seed=5)).cuda()
+    vals = A.vals
+    vals.requires_grad_(True)
+    x = P.SpTRSVFunction.apply(vals, b, plan)
+    (x * w).sum().backward()
+    gv, gb = vals.grad.detach().clone(), b.grad.detach().clone()
+    vals.requires_grad_(False)
+
+    def loss(bb):
+        with torch.no_grad():
+            return float((plan.solve(bb) * w).sum())
+
+    rng = np.random.default_rng(0)
+    for p in rng.choice(A_h.nnz, size=24, replace=False):
+        h = 1e-6 * max(1.0, abs(float(A.vals[p])))
+        old = float(A.vals[p])
+        with torch.no_grad():
+            A.vals[p] = old + h
+            fp = loss(b.detach())
+            A.vals[p] = old - h
+            fm = loss(b.detach())
+            A.vals[p] = old
+        fd = (fp - fm) / (2 * h)
+        assert abs(fd - float(gv[p])) <= 1e-6 * max(1.0, abs(float(gv[p])))
+    for (i, r) in [(0, 0), (17, 3), (1000, 7), (4095, 1), (2047, 5)]:
+        bp, bm = b.detach().clone(), b.detach().clone()
+        bp[i, r] += 1e-6
+        bm[i, r] -= 1e-6
+        fd = (loss(bp) - loss(bm)) / 2e-6
+        assert abs(fd - float(gb[i, r])) <= 1e-6 * max(1.0, abs(float(gb[i, r])))
+    # and against the oracle gradient
+    gref = oracle.solve_transpose(A_h, w.cpu().numpy())
+    assert relerr(gb.cpu().numpy(), gref) <= 1e-12
+    xref = oracle.solve(A_h, b.detach().cpu().numpy())
+    assert relerr(gv.cpu().numpy(), oracle.grad_vals(A_h, gref, xref)) <= 1e-12
+
+
+@pytest.mark.parametrize("dt", [np.float64, np.float32], ids=["f64", "f32"])
+def test_full_size_lap2d(dt):
+    import paper_2609_40159_gb300 as P
+    A_h = S.lap2d(1024, dtype=dt)
+    b_h = S.rhs(A_h.n, 1, seed=1, dtype=dt)
+    x_ref = oracle.solve(widened(A_h), b_h)
+    A = P.Matrix.from_host(A_h)
+    b = torch.as_tensor(b_h).cuda()
+    plan = P.Plan(A, transpose=True)
+    for mode in MODES:
+        plan.set(mode, 32, 1)
+        assert relerr(plan.solve(b).cpu().numpy(), x_ref) <= TOL[dt], mode
+    assert P.handle().status() == 0
+
+
+def test_full_size_lap3d_fwd_bwd():
+    import paper_2609_40159_gb300 as P
+    A_h = S.lap3d(128)
+    b_h = S.rhs(A_h.n, 8, seed=4)
+    w_h = S.rhs(A_h.n, 8, seed=5)
+    A = P.Matrix.from_host(A_h)
+    plan = P.Plan(A, transpose=True)
+    x_ref = oracle.solve(A_h, b_h)
+    g_ref = oracle.solve_transpose(A_h, w_h)
+    b, w = torch.as_tensor(b_h).cuda(), torch.as_tensor(w_h).cuda()
+    for mode in ["level", "syncfree", "block"]:
+        plan.set(mode, 32, 8)
+        x = plan.solve(b)
+        assert relerr(x.cpu().numpy(), x_ref) <= 1e-12, mode
+        gb = plan.solve_transpose(w)
+        assert relerr(gb.cpu().numpy(), g_ref) <= 1e-12, mode
+    gv = plan.grad_vals(gb, x).cpu().numpy()
+    rng = np.random.default_rng(1)
+    rows = np.repeat(np.arange(A_h.n), np.diff(A_h.row_ptr))
+    for p in rng.choice(A_h.nnz, size=2000, replace=False):
+        ref = -np.dot(g_ref[rows[p]], x_ref[A_h.col_idx[p]])
+        assert abs(gv[p] - ref) <= 1e-12 * max(1.0, abs(ref))
+
+
+def test_full_size_powerlaw():
+    import paper_2609_40159_gb300 as P
+    A_h = S.powerlaw(4_000_000, alpha=2.1, seed=2)
+    b_h = S.rhs(A_h.n, 1, seed=2)
+    x_ref = oracle.solve(A_h, b_h)
+    A = P.Matrix.from_host(A_h)
+    b = torch.as_tensor(b_h).cuda()
+    plan = P.Plan(A)
+    for mode, rpw in [("level", 32), ("syncfree", 32), ("syncfree", 4), ("block", 32)]:
+        plan.set(mode, rpw, 1)
+        assert relerr(plan.solve(b).cpu().numpy(), x_ref) <= 1e-12, mode
+
+
+@pytest.mark.parametrize("mode", ["syncfree", "block"])
+def test_bounded_wait_reports_timeout(mode):
+    import paper_2609_40159_gb300 as P
+    A_h = S.chain(5000, seed=1)
+    A = P.Matrix.from_host(A_h)
+    b = torch.as_tensor(S.rhs(A_h.n, 1, seed=1)).cuda()
+    plan = P.Plan(A, mode=mode, spin_limit=1 << 12)
+    h = P.handle()
+    assert h.status() == 0
+    plan.withhold(100)      # row 100's ready flag is never released
+    plan.solve(b)
+    assert h.status() == P._lib.SPTRSV_ETIMEOUT
+    plan.withhold(-1)
+    x = plan.solve(b)
+    assert h.status() == 0
+    assert relerr(x.cpu().numpy(), oracle.solve(A_h, b.cpu().numpy())) <= 1e-12
+
+
+def test_cuda_graph_replay():
+    import paper_2609_40159_gb300 as P
+    A_h = S.band_random(50_000, 64, 4, 16, seed=11)
+    A = P.Matrix.from_host(A_h)
+    b = torch.as_tensor(S.rhs(A_h.n, 2, seed=3)).cuda()
+    x = torch.empty_like(b)
+    for mode in ["level", "syncfree", "block"]:
+        plan = P.Plan(A, mode=mode)
+        plan.solve(b, out=x)  # warm-up outside capture
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        s = torch.cuda.Stream()
+        with torch.cuda.stream(s):
+            plan_s = P.Plan(A, mode=mode)
+            plan_s.solve(b, out=x)
+            torch.cuda.synchronize()
+            with torch.cuda.graph(g, stream=s):
+                plan_s.solve(b, out=x)
+        for _ in range(3):
+            x.zero_()
+            g.replay()
+            torch.cuda.synchronize()
+            assert relerr(x.cpu().numpy(), oracle.solve(A_h, b.cpu().numpy())) <= 1e-12, mode
