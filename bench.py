@@ -1,0 +1,501 @@
+#!/usr/bin/env python
+"""Benchmark of the SpTRSV hot path on GB300.
+
+Workload (one step): 512 independent lower-triangular CSR systems (n log-
+uniform in [1e3, 2e5], band log-uniform in [16, 1024], 4-16 off-diagonals
+per row, FP32 values, 1-32 right-hand sides, odd-indexed systems rewritten
+by the narrowest-level rule with chunks of 8 levels); one step is the
+batched forward solve x = L^{-1} (b [+ T b]) plus its adjoint: transpose
+solve g_b' = L^{-T} w, T^T application and the value gradient on L's
+pattern.  Analysis and rewriting are the preprocessing step of the method
+(done once, timed and reported separately).
+
+Printed (rank 0): ONE JSON line with value = algorithmic GB/s of the whole
+step over all ranks, the dominant kernel's roofline, the plain level-set
+baseline (one launch per level, per system, original DAG), a single-system
+section (2D Laplacian 1024^2) and the CPU oracle timed on the host.
+``--impl reference`` times the CPU oracle on the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synthetic as S  # noqa: E402
+
+METRIC = "SpTRSV GB/s & % HBM peak: batched fwd+adjoint vs plain level-set solve"
+WORKLOAD = ("batch512: 512 banded lower-triangular CSR systems, n~logU[1e3,2e5], "
+            "band~logU[16,1024], 4-16 offdiag/row, FP32, 1-32 RHS; odd systems rewritten "
+            "(narrowest-level 1%, D=8); step = batched fwd solve + adjoint "
+            "(transpose solve, T^T, value gradient)")
+FALLBACK_HBM = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--nmat", type=int, default=512)
+    ap.add_argument("--no-extras", action="store_true", help="skip baseline/single/cpu legs")
+    ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--ncu", action="store_true", help="minimal run for a profiler launch list")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ bytes
+def bytes_fwd(n, nnz, k, wv, tn=0, tnnz=0):
+    """Algorithmic bytes of one forward solve: L once (values + column
+    indices + row pointers), b read, x written (x gathers assumed cached),
+    plus T for a rewritten system."""
+    b = nnz * (wv + 4) + (n + 1) * 4 + 2 * n * k * wv
+    if tn:
+        b += tnnz * (wv + 4) + (tn + 1) * 4
+    return b
+
+
+def bytes_bwd(n, nnz, k, wv, tn=0, tnnz=0):
+    """Transpose solve (L^T once, g_x read, g_b' written), value gradient
+    (column indices, row pointers, g_b' and x read, gradient written) and,
+    for a rewritten system, T^T (T once, g_b' read, g_b written)."""
+    b = nnz * (wv + 4) + (n + 1) * 4 + 2 * n * k * wv
+    b += nnz * 4 + (n + 1) * 4 + 2 * n * k * wv + nnz * wv
+    if tn:
+        b += tnnz * (wv + 4) + (tn + 1) * 4 + 2 * n * k * wv
+    return b
+
+
+def hbm_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM, "fallback"
+
+
+# ----------------------------------------------------------------- clocks
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return dict(sm_mhz=None, sm_max_mhz=None, reasons=["nvidia-smi unavailable"])
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() in ("active", "yes", "1"):
+                    reasons.add(nm)
+        return dict(sm_mhz=float(np.median(sm)) if sm else None,
+                    sm_max_mhz=float(max(mx)) if mx else None,
+                    samples=len(sm), reasons=sorted(reasons))
+
+
+# ------------------------------------------------------------- reference
+def run_reference(args, items, rank):
+    """The CPU oracle on the same workload: every step is a bounded sample
+    (a rotating slice of the systems) of fwd solve + adjoint in FP64."""
+    import oracle
+    nmat = len(items)
+    per = max(1, nmat // 8)
+    wv = 4
+    prepared = []
+    for m, it in enumerate(items):
+        A = S.CSR(it.A.n, it.A.row_ptr, it.A.col_idx, it.A.vals.astype(np.float64))
+        prepared.append(A)
+
+    def step(s):
+        ms = [(s * per + q) % nmat for q in range(per)]
+        t0 = time.perf_counter()
+        nb = 0
+        for m in ms:
+            A, it = prepared[m], items[m]
+            x = oracle.solve(A, it.b)
+            g = oracle.solve_transpose(A, it.b)
+            oracle.grad_vals(A, g, x)
+            nb += bytes_fwd(A.n, A.nnz, it.nrhs, wv) + bytes_bwd(A.n, A.nnz, it.nrhs, wv)
+        return time.perf_counter() - t0, nb
+
+    for s in range(args.warmup):
+        step(s)
+    tt, bb = 0.0, 0
+    for s in range(args.steps):
+        t, b = step(args.warmup + s)
+        tt += t
+        bb += b
+    gbs = bb / tt / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": gbs, "unit": "GB/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "reference": "CPU oracle (no reference code exists)"},
+        "cpu_baseline": {"kind": "oracle", "value": gbs, "unit": "GB/s", "cores": 1,
+                         "sample": f"{per} of {nmat} systems per step (rotating), fwd + transpose "
+                                   "solve + value gradient, FP64 on widened FP32 values"},
+        "e2e": {"value": gbs, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ ours
+def build_batch(P, items, dev):
+    """Device systems (rewrites of the marked ones), packed RHS."""
+    import torch
+    t_an = t_rw = 0.0
+    mats, Ts, levels = [], [], []
+    for it in items:
+        A = P.Matrix.from_host(it.A, device=dev)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        an = P.analyze(A)
+        t_an += time.perf_counter() - t0
+        lv = [an.nlevels, an.nlevels]
+        T = None
+        if it.rewritten:
+            t0 = time.perf_counter()
+            rows, tg = S.narrowest_levels_list(an.nlevels, an.level_ptr.cpu().numpy(),
+                                               an.perm.cpu().numpy(), 0.01, 8)
+            A2, T = P.rewrite(A, an.lev, rows, tg)
+            t_rw += time.perf_counter() - t0
+            lv[1] = P.analyze(A2).nlevels
+            A = A2
+        mats.append(A)
+        Ts.append(T)
+        levels.append(lv)
+    return mats, Ts, levels, t_an, t_rw
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    # inputs are drawn before CUDA is touched (spawned worker pool)
+    items = S.batch_spec_parallel(nmat=args.nmat, seed=3 + 1000 * rank)
+    if args.impl == "reference":
+        if rank == 0:
+            run_reference(args, items, rank)
+        return
+
+    import torch
+    import paper_2609_40159_gb300 as P
+    from paper_2609_40159_gb300 import autotune
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    t0 = time.perf_counter()
+    mats, Ts, levels, t_an, t_rw = build_batch(P, items, dev)
+    nrhs = [it.nrhs for it in items]
+    t1 = time.perf_counter()
+    bplan = P.BatchPlan(mats, Ts, nrhs, transpose=True)
+    t_plan = time.perf_counter() - t1
+    t_prep = time.perf_counter() - t0
+
+    b = torch.cat([torch.as_tensor(it.b).reshape(-1) for it in items]).to(dev)
+    gen = torch.Generator(device=dev).manual_seed(5 + rank)
+    w = torch.rand(b.numel(), generator=gen, device=dev, dtype=torch.float32) * 2 - 1
+    x, gbp, gb = torch.empty_like(b), torch.empty_like(b), torch.empty_like(b)
+    gv = torch.empty(bplan.total_nnz, dtype=torch.float32, device=dev)
+
+    tune = None
+    if not args.no_tune and not args.ncu:
+        tune = autotune.tune_batch(bplan, b, candidates=(8, 16, 32), reps=3)
+
+    # algorithmic bytes
+    wv = 4
+    bf = bb = 0
+    for A, T, k in zip(mats, Ts, nrhs):
+        tn, tnnz = (A.n, T.nnz) if T is not None else (0, 0)
+        bf += bytes_fwd(A.n, A.nnz, k, wv, tn, tnnz)
+        bb += bytes_bwd(A.n, A.nnz, k, wv, tn, tnnz)
+    b_solveT = sum(A.nnz * (wv + 4) + (A.n + 1) * 4 + 2 * A.n * k * wv for A, k in zip(mats, nrhs))
+    step_bytes = bf + bb
+
+    # three graphs per step: forward, transpose solve, T^T + gradient
+    s = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(s):
+        gplan = P.BatchPlan(mats, Ts, nrhs, transpose=True)
+        if tune is not None:
+            gplan.set_rows_per_warp([tune["choice"][l] for l in autotune.batch_classes(gplan)])
+        for _ in range(2):
+            gplan.solve(b, out=x)
+            gplan.solve_transpose(w, out=gbp)
+            gplan.tt_apply(gbp, out=gb)
+            gplan.grad_vals(gbp, x, out=gv)
+        torch.cuda.synchronize()
+        g_f, g_t, g_r = torch.cuda.CUDAGraph(), torch.cuda.CUDAGraph(), torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g_f, stream=s):
+            gplan.solve(b, out=x)
+        with torch.cuda.graph(g_t, stream=s):
+            gplan.solve_transpose(w, out=gbp)
+        with torch.cuda.graph(g_r, stream=s):
+            gplan.tt_apply(gbp, out=gb)
+            gplan.grad_vals(gbp, x, out=gv)
+    torch.cuda.synchronize()
+    if P.handle().status() != 0:
+        raise RuntimeError("device status after set-up")
+
+    def step():
+        g_f.replay()
+        g_t.replay()
+        g_r.replay()
+
+    with torch.cuda.stream(s):
+        for _ in range(args.warmup):
+            step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    K = args.steps
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(K)]
+    clk = Clocks(local)
+    clk.start()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(s):
+        for k in range(K):
+            ev[k][0].record(s)
+            g_f.replay()
+            ev[k][1].record(s)
+            g_t.replay()
+            ev[k][2].record(s)
+            g_r.replay()
+            ev[k][3].record(s)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    if dist:
+        dist.barrier()
+    tot_ms = ev[0][0].elapsed_time(ev[K - 1][3])
+    f_ms = float(np.mean([e[0].elapsed_time(e[1]) for e in ev]))
+    t_ms = float(np.mean([e[1].elapsed_time(e[2]) for e in ev]))
+    r_ms = float(np.mean([e[2].elapsed_time(e[3]) for e in ev]))
+    ms_step = tot_ms / K
+    if dist:
+        tm = torch.tensor([ms_step], device=dev)
+        dist.all_reduce(tm, op=dist.ReduceOp.MAX)
+        ms_step = float(tm.item())
+    value = world * step_bytes / (ms_step * 1e-3) / 1e9
+    status = P.handle().status()
+
+    # correctness spot check of the timed buffers on two systems (device only)
+    if rank == 0 and status != 0:
+        raise RuntimeError(f"device status {status} after timed region")
+
+    # roofline of the dominant kernel (forward or transpose batched solve)
+    peak, peak_kind = hbm_peak()
+    if f_ms >= t_ms:
+        dom, dom_bytes, dom_ms = "k_batch<float,false> (forward batched solve)", bf, f_ms
+    else:
+        dom, dom_bytes, dom_ms = "k_batch<float,true> (transpose batched solve)", b_solveT, t_ms
+    achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(tpath) as f:
+            tj = json.load(f)
+        key = "fwd" if f_ms >= t_ms else "trans"
+        import hashlib
+        h = hashlib.sha256()
+        for fn in ("block.cuh", "batch.cu", "rows.cuh", "common.cuh"):
+            with open(os.path.join(ROOT, "paper_2609_40159_gb300", "csrc", fn), "rb") as fh:
+                h.update(fh.read())
+        if tj.get("source_sha256") == h.hexdigest() and key in tj:
+            traffic = tj[key]["bytes_per_launch_full_scale"]
+    except Exception:
+        traffic = None
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic, "algorithmic_bytes": dom_bytes, "ms_per_launch": dom_ms}
+
+    # end to end through the C ABI with host buffers
+    e2e = None
+    if not args.ncu:
+        pin = lambda t: torch.empty(t.numel(), dtype=t.dtype, pin_memory=True)
+        hb, hw, hx, hgb, hgv = pin(b), pin(w), pin(x), pin(gb), pin(gv)
+        hb.copy_(b.cpu())
+        hw.copy_(w.cpu())
+        torch.cuda.synchronize()
+        Ke = max(2, min(K, 5))
+        with torch.cuda.stream(s):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            for _ in range(Ke):
+                b.copy_(hb, non_blocking=True)
+                w.copy_(hw, non_blocking=True)
+                step()
+                hx.copy_(x, non_blocking=True)
+                hgb.copy_(gb, non_blocking=True)
+                hgv.copy_(gv, non_blocking=True)
+            e1.record(s)
+        torch.cuda.synchronize()
+        e2e_ms = e0.elapsed_time(e1) / Ke
+        e2e = {"value": world * step_bytes / (e2e_ms * 1e-3) / 1e9, "unit": "GB/s",
+               "ms_per_step": e2e_ms,
+               "h2d_bytes_per_step": int(hb.numel() * 4 + hw.numel() * 4),
+               "d2h_bytes_per_step": int(hx.numel() * 4 + hgb.numel() * 4 + hgv.numel() * 4)}
+
+    extras = {}
+    if rank == 0 and not args.no_extras and not args.ncu:
+        extras = run_extras(P, items, mats, dev, bf)
+
+    if rank == 0:
+        nlev = np.array(levels)
+        line = {
+            "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": K,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "systems_per_gpu": len(items),
+                       "rows_per_gpu": int(sum(A.n for A in mats)),
+                       "nnz_per_gpu": int(sum(A.nnz for A in mats)),
+                       "rhs_per_gpu": int(sum(it.nrhs * it.A.n for it in items)),
+                       "l2": "inputs 3.3 GB >> 129 MB L2; no flush needed",
+                       "timing": "CUDA events on the launching stream around 3 CUDA-graph "
+                                 "replays per step (fwd | transpose | T^T + gradient)",
+                       "parallelism": f"dp{world} (independent batches per GPU, no collective)"},
+            "gb_per_step": step_bytes / 1e9,
+            "solves_per_s": world * len(items) / (ms_step * 1e-3),
+            "phase_ms": {"fwd": f_ms, "transpose": t_ms, "tt_and_grad": r_ms},
+            "fwd_only_gbs": bf / (f_ms * 1e-3) / 1e9,
+            "levels": {"max_orig": int(nlev[:, 0].max()), "max_rewritten": int(nlev[1::2, 1].max()),
+                       "sum_orig": int(nlev[:, 0].sum()), "sum_after": int(nlev[:, 1].sum())},
+            "preprocess_s": {"analyze": t_an, "rewrite": t_rw, "plan": t_plan, "total": t_prep},
+            "autotune": None if tune is None else {"choice": tune["choice"], "ms": tune["ms"]},
+            "roofline": roofline,
+            "clocks": clocks,
+            "gpu_launches": 6 * K,
+            "e2e": e2e,
+        }
+        line.update(extras)
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def run_extras(P, items, mats, dev, bf_total):
+    """Plain level-set baseline, a single-system comparison and the CPU
+    oracle, all on rank 0."""
+    import torch
+    import oracle
+    from paper_2609_40159_gb300 import autotune
+    out = {}
+    # --- plain level-set solve, one launch per level, original DAG, per system
+    sub = list(range(0, len(items), 16))
+    wv = 4
+    plans, bs, nbytes = [], [], 0
+    for m in sub:
+        A = P.Matrix.from_host(items[m].A, device=dev)
+        plans.append(P.Plan(A, mode="level_launch"))
+        bs.append(torch.as_tensor(items[m].b).to(dev))
+        nbytes += bytes_fwd(A.n, A.nnz, items[m].nrhs, wv)
+    for p, bb in zip(plans[:2], bs[:2]):
+        p.solve(bb)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for p, bb in zip(plans, bs):
+        p.solve(bb)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    out["baseline_plain_level_set"] = {
+        "gbs": nbytes / (ms * 1e-3) / 1e9, "solves_per_s": len(sub) / (ms * 1e-3),
+        "ms": ms, "sample": f"{len(sub)} of {len(items)} systems (every 16th), forward only, "
+                            "original DAG, one kernel launch per level, host loop over systems",
+        "levels_launched": int(sum(p.info()["nlevels"] for p in plans))}
+    del plans
+    # --- single system: 2D Laplacian 1024^2, FP64, every mode, original and rewritten
+    A_h = S.lap2d(1024)
+    A = P.Matrix.from_host(A_h, device=dev)
+    an = P.analyze(A)
+    rows, tg = S.narrowest_levels_list(an.nlevels, an.level_ptr.cpu().numpy(), an.perm.cpu().numpy(), 0.01, 8)
+    Lp, T = P.rewrite(A, an.lev, rows, tg)
+    an2 = P.analyze(Lp)
+    b = torch.as_tensor(S.rhs(A_h.n, 1, seed=1)).to(dev)
+    x = torch.empty_like(b)
+    res = {"levels_orig": an.nlevels, "levels_rewritten": an2.nlevels,
+           "cv_cost_orig": float(an.stats[3]), "cv_cost_rewritten": float(an2.stats[3]),
+           "rows_rewritten": int(len(rows)), "nnz_T": int(T.nnz), "nnz_Lp": int(Lp.nnz)}
+    modes = {}
+    for name, (M, TT) in {"orig": (A, None), "rewritten": (Lp, T)}.items():
+        p = P.Plan(M, TT)
+        nb = bytes_fwd(M.n, M.nnz, 1, 8, M.n if TT is not None else 0, TT.nnz if TT is not None else 0)
+        for mode in ("level_launch", "level", "syncfree", "block"):
+            p.set(mode, 32, 1)
+            ms = autotune.time_call(lambda: p.solve(b, out=x), reps=5, warmup=2)
+            modes[f"{name}:{mode}"] = {"us": 1e3 * ms, "gbs": nb / (ms * 1e-3) / 1e9}
+    res["fwd"] = modes
+    out["single_lap2d_1024_f64"] = res
+    # --- CPU oracle on the host cores (whole batch, fwd + adjoint, one pass)
+    t0 = time.perf_counter()
+    nb = 0
+    for it in items:
+        A64 = S.CSR(it.A.n, it.A.row_ptr, it.A.col_idx, it.A.vals.astype(np.float64))
+        xx = oracle.solve(A64, it.b)
+        g = oracle.solve_transpose(A64, it.b)
+        oracle.grad_vals(A64, g, xx)
+        nb += bytes_fwd(A64.n, A64.nnz, it.nrhs, 4) + bytes_bwd(A64.n, A64.nnz, it.nrhs, 4)
+    dt = time.perf_counter() - t0
+    out["cpu_baseline"] = {"value": nb / dt / 1e9, "unit": "GB/s", "cores": 1,
+                           "cores_available": os.cpu_count(), "kind": "oracle", "seconds": dt,
+                           "sample": f"all {len(items)} systems, one fwd solve + transpose solve "
+                                     "+ value gradient (no rewrite), FP64 on widened FP32 values"}
+    return out
+
+
+if __name__ == "__main__":
+    main()

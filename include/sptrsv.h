@@ -98,7 +98,9 @@ typedef struct {
     int32_t rows_per_warp;   /* 1,2,4,8,16,32 (lanes per row = 32/rows_per_warp); 0 = auto */
     int32_t rhs_tile;        /* right-hand sides per pass: 1,2,4,8,16; 0 = auto */
     int32_t build_transpose; /* non-zero: prepare sptrsv_solve_transpose / grad  */
-    int64_t spin_limit;      /* polls before a device wait gives up; 0 = default */
+    int64_t wait_limit_us;   /* longest a device wait may take before the solve
+                                gives up with SPTRSV_ETIMEOUT (microseconds);
+                                0 = default (10 s)                            */
 } sptrsv_plan_opts;
 
 typedef struct sptrsv_handle_st *sptrsv_handle;
@@ -203,6 +205,10 @@ sptrsv_status sptrsv_batch_plan_create(sptrsv_handle handle, int32_t nmat, const
                                        const sptrsv_csr *Ts, const int32_t *nrhs,
                                        const sptrsv_plan_opts *opts, sptrsv_plan *plan);
 sptrsv_status sptrsv_batch_offsets(sptrsv_plan plan, int64_t *rhs_offset, int64_t *vals_offset);
+/* Re-tunes a batched plan: rows_per_warp (host, nmat entries; 0 = keep) is
+ * the row-group width of every system (used by the autotuner; no analysis
+ * is repeated).  Synchronises.                                             */
+sptrsv_status sptrsv_batch_plan_set(sptrsv_plan plan, const int32_t *rows_per_warp);
 /* All systems in one persistent launch (plus a tiny reset launch): no host
  * work per matrix, so the call can be captured in a CUDA graph.            */
 sptrsv_status sptrsv_batch_solve(sptrsv_plan plan, const void *b, void *x);
@@ -214,7 +220,7 @@ sptrsv_status sptrsv_batch_tt_apply(sptrsv_plan plan, const void *gbp, void *gb)
 /* ------------------------------------------------------------- diagnostics */
 /* Test hook for the bounded waits: makes the next solves of `plan` skip
  * publishing row `row` (-1 clears it), so that any row waiting on it gives
- * up after spin_limit polls and the solve reports SPTRSV_ETIMEOUT.          */
+ * up after wait_limit_us and the solve reports SPTRSV_ETIMEOUT.            */
 sptrsv_status sptrsv_debug_withhold_row(sptrsv_plan plan, int32_t row);
 
 #ifdef __cplusplus

@@ -162,10 +162,10 @@ class Plan:
     """Reusable solve plan for L (and T of a rewritten system)."""
 
     def __init__(self, A: Matrix, T: Matrix | None = None, mode="auto", rows_per_warp=0,
-                 rhs_tile=0, transpose=False, spin_limit=0):
+                 rhs_tile=0, transpose=False, wait_limit_us=0):
         self.A, self.T = A, T
         opts = L.sptrsv_plan_opts(L.MODE_NAMES[mode] if isinstance(mode, str) else int(mode),
-                                  rows_per_warp, rhs_tile, 1 if transpose else 0, spin_limit)
+                                  rows_per_warp, rhs_tile, 1 if transpose else 0, wait_limit_us)
         p = L.sptrsv_plan()
         self._h = handle()
         tdesc = T.desc() if T is not None else None
@@ -240,7 +240,7 @@ class BatchPlan:
     """One plan over many independent systems; right-hand sides, solutions
     and gradients are packed (see sptrsv_batch_plan_create)."""
 
-    def __init__(self, mats, Ts=None, nrhs=None, rows_per_warp=None, transpose=False, spin_limit=0):
+    def __init__(self, mats, Ts=None, nrhs=None, rows_per_warp=None, transpose=False, wait_limit_us=0):
         nmat = len(mats)
         self.mats, self.Ts = list(mats), list(Ts) if Ts is not None else [None] * nmat
         self.nrhs = [int(k) for k in (nrhs if nrhs is not None else [1] * nmat)]
@@ -252,7 +252,7 @@ class BatchPlan:
             T = self.Ts[m]
             tdescs[m] = T.desc() if T is not None else L.sptrsv_csr(0, 0, None, None, None, 0)
             rpw = 0 if rows_per_warp is None else int(rows_per_warp[m] if hasattr(rows_per_warp, "__len__") else rows_per_warp)
-            opts[m] = L.sptrsv_plan_opts(L.SPTRSV_MODE_BLOCK, rpw, 0, 1 if transpose else 0, spin_limit)
+            opts[m] = L.sptrsv_plan_opts(L.SPTRSV_MODE_BLOCK, rpw, 0, 1 if transpose else 0, wait_limit_us)
         ks = (C.c_int32 * max(nmat, 1))(*self.nrhs)
         self._h = handle()
         p = L.sptrsv_plan()
@@ -265,6 +265,13 @@ class BatchPlan:
         self.rhs_offset = np.array(list(ro), dtype=np.int64)
         self.vals_offset = np.array(list(vo), dtype=np.int64)
         self.dtype = mats[0].dtype if nmat else torch.float32
+
+    def set_rows_per_warp(self, rpw):
+        """Row-group width per system (list) or for all systems (int)."""
+        nmat = len(self.mats)
+        vals = [int(rpw)] * nmat if not hasattr(rpw, "__len__") else [int(r) for r in rpw]
+        arr = (C.c_int32 * max(nmat, 1))(*vals)
+        L.check(L.lib().sptrsv_batch_plan_set(self.p, arr), "sptrsv_batch_plan_set")
 
     @property
     def total_rhs(self):

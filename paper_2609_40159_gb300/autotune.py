@@ -1,0 +1,145 @@
+"""Autotuner for the solve schedule.
+
+For a single-system plan it times every candidate (mode, rows per warp, rhs
+tile) with CUDA events and keeps the fastest; for a batched plan it picks the
+rows-per-warp of every size class (bucketed average row length and number of
+right-hand sides) by coordinate descent over the classes.  Winners are cached
+in a JSON file keyed by size class (``SPTRSV_TUNE_CACHE`` or
+``~/.cache/sptrsv_gb300/tune.json``).
+"""
+from __future__ import annotations
+
+import json
+import math
+import os
+
+import numpy as np
+import torch
+
+from .api import BatchPlan, Plan
+
+CANDIDATE_MODES = ("level", "syncfree", "block")
+CANDIDATE_RPW = (1, 4, 8, 16, 32)
+
+
+def _cache_path():
+    p = os.environ.get("SPTRSV_TUNE_CACHE")
+    if p:
+        return p
+    return os.path.join(os.path.expanduser("~"), ".cache", "sptrsv_gb300", "tune.json")
+
+
+def _load_cache():
+    try:
+        with open(_cache_path()) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def _store_cache(c):
+    p = _cache_path()
+    try:
+        os.makedirs(os.path.dirname(p), exist_ok=True)
+        with open(p + ".tmp", "w") as f:
+            json.dump(c, f, indent=1, sort_keys=True)
+        os.replace(p + ".tmp", p)
+    except OSError:
+        pass
+
+
+def _bucket(v):
+    return int(round(math.log2(max(v, 1e-9)))) if v > 0 else -99
+
+
+def size_class(n, nnz, nlevels, k, dtype) -> str:
+    """Size class of a system: log2 buckets of n, row length, level width, k."""
+    width = n / max(nlevels, 1)
+    return (f"{str(dtype).split('.')[-1]}:n{_bucket(n)}:r{_bucket(nnz / max(n, 1))}"
+            f":w{_bucket(width)}:k{_bucket(k)}")
+
+
+def time_call(fn, reps=5, warmup=2) -> float:
+    """Median milliseconds of fn() on the current stream (CUDA events)."""
+    for _ in range(warmup):
+        fn()
+    s = torch.cuda.current_stream()
+    ts = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(s)
+        fn()
+        b.record(s)
+        b.synchronize()
+        ts.append(a.elapsed_time(b))
+    return float(np.median(ts))
+
+
+def tune_plan(plan: Plan, b: torch.Tensor, modes=CANDIDATE_MODES, rpws=CANDIDATE_RPW,
+              kts=None, use_cache=True, reps=5):
+    """Times every candidate on the right-hand side b and applies the best."""
+    n, k = plan.A.n, (b.shape[1] if b.dim() == 2 else 1)
+    info = plan.info()
+    key = size_class(n, plan.A.nnz, info["nlevels"], k, plan.A.dtype)
+    cache = _load_cache() if use_cache else {}
+    if key in cache:
+        c = cache[key]
+        plan.set(c["mode"], c["rows_per_warp"], c["rhs_tile"])
+        return dict(key=key, best=c, cached=True, table=[])
+    if kts is None:
+        kts = [t for t in (1, 2, 4, 8, 16) if t <= max(1, 1 << math.ceil(math.log2(k)))] or [1]
+    x = torch.empty(n, k, dtype=b.dtype, device=b.device)
+    b2 = b.view(n, k)
+    table = []
+    for mode in modes:
+        for rpw in rpws:
+            for kt in kts:
+                plan.set(mode, rpw, kt)
+                ms = time_call(lambda: plan.solve(b2, out=x), reps=reps)
+                table.append(dict(mode=mode, rows_per_warp=rpw, rhs_tile=kt, ms=ms))
+    best = min(table, key=lambda r: r["ms"])
+    plan.set(best["mode"], best["rows_per_warp"], best["rhs_tile"])
+    if use_cache:
+        cache = _load_cache()
+        cache[key] = best
+        _store_cache(cache)
+    return dict(key=key, best=best, cached=False, table=table)
+
+
+def batch_classes(bplan: BatchPlan):
+    """Size class label (average row length bucket, k bucket) of each system."""
+    labels = []
+    for A, k in zip(bplan.mats, bplan.nrhs):
+        labels.append(f"r{_bucket(A.nnz / max(A.n, 1))}:k{_bucket(k)}")
+    return labels
+
+
+def tune_batch(bplan: BatchPlan, b: torch.Tensor, candidates=(8, 16, 32), reps=3, rounds=1):
+    """Per size class rows-per-warp for the batched solve (coordinate descent:
+    each class tries every candidate with the others fixed)."""
+    labels = batch_classes(bplan)
+    classes = sorted(set(labels))
+    choice = {c: 32 for c in classes}
+    x = torch.empty_like(b)
+
+    def apply():
+        bplan.set_rows_per_warp([choice[l] for l in labels])
+
+    apply()
+    best_ms = time_call(lambda: bplan.solve(b, out=x), reps=reps)
+    log = [dict(step="start", ms=best_ms)]
+    for _ in range(rounds):
+        for c in classes:
+            keep = choice[c]
+            for cand in candidates:
+                if cand == keep:
+                    continue
+                choice[c] = cand
+                apply()
+                ms = time_call(lambda: bplan.solve(b, out=x), reps=reps)
+                log.append(dict(cls=c, rpw=cand, ms=ms))
+                if ms < best_ms * 0.995:
+                    best_ms, keep = ms, cand
+            choice[c] = keep
+            apply()
+    return dict(choice=choice, ms=best_ms, log=log)

@@ -102,14 +102,11 @@ k_levels(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, int32_t
                     } else {
                         lj = ld_relaxed(lev + j);
                         if (lj < 0) {
-                            long long polls = 0;
+                            WaitClock clk;
                             for (;;) {
                                 lj = ld_relaxed(lev + j);
                                 if (lj >= 0) break;
-                                if ((++polls & 255) == 0) {
-                                    if (aborted(w)) { failed = true; break; }
-                                    if (polls >= w.limit) { give_up(w); failed = true; break; }
-                                }
+                                if (clk.expired(w)) { failed = true; break; }
                             }
                             if (failed) break;
                         }
@@ -250,7 +247,7 @@ cudaError_t launch_validate(const sptrsv_csr &L, long long *out_dev, cudaStream_
     return cudaGetLastError();
 }
 
-cudaError_t launch_levels(const sptrsv_csr &L, int32_t *lev, const Ctl &ctl, long long spin_limit,
+cudaError_t launch_levels(const sptrsv_csr &L, int32_t *lev, const Ctl &ctl, long long limit_ns,
                           const DeviceInfo &di, cudaStream_t s)
 {
     if (L.n <= 0) return cudaSuccess;
@@ -263,7 +260,7 @@ cudaError_t launch_levels(const sptrsv_csr &L, int32_t *lev, const Ctl &ctl, lon
     int64_t blocks = (int64_t)per_sm * di.num_sms;
     const int64_t need = (chunks + kLevWarps - 1) / kLevWarps;
     if (blocks > need) blocks = need;
-    Waiter w{ctl.status, ctl.abort_flag, spin_limit};
+    Waiter w{ctl.status, ctl.abort_flag, limit_ns};
     k_levels<<<(int)blocks, kLevThreads, 0, s>>>(L.row_ptr, L.col_idx, L.n, lev, ctl.counters, w);
     return cudaGetLastError();
 }

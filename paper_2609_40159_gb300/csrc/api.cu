@@ -1,6 +1,8 @@
 // C ABI of the SpTRSV library (declared in include/sptrsv.h): handles, plans,
 // level analysis, rewriting, single and batched solves, adjoints.
 #include <algorithm>
+#include <cstdio>
+#include <cstdlib>
 #include <climits>
 #include <cstring>
 #include <new>
@@ -12,13 +14,34 @@
 using namespace spt;
 
 namespace {
-constexpr long long kDefaultSpin = 1ll << 22;
+constexpr long long kDefaultWaitNs = 10ll * 1000 * 1000 * 1000;  // 10 s
+
+bool debug_mode()
+{
+    static int on = -1;
+    if (on < 0) {
+        const char *v = getenv("SPTRSV_DEBUG");
+        on = (v && v[0] && v[0] != '0') ? 1 : 0;
+    }
+    return on == 1;
+}
 
 sptrsv_status from_cuda(cudaError_t e)
 {
     if (e == cudaSuccess) return SPTRSV_OK;
+    if (debug_mode()) fprintf(stderr, "[sptrsv] CUDA error: %s\n", cudaGetErrorString(e));
     cudaGetLastError();
     return e == cudaErrorMemoryAllocation ? SPTRSV_ENOMEM : SPTRSV_ECUDA;
+}
+
+// With SPTRSV_DEBUG set, every asynchronous entry point synchronises so that
+// a failing kernel is reported by the call that launched it.
+sptrsv_status debug_sync(sptrsv_status st, cudaStream_t s, const char *what)
+{
+    if (st != SPTRSV_OK || !debug_mode()) return st;
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) fprintf(stderr, "[sptrsv] %s: %s\n", what, cudaGetErrorString(e));
+    return from_cuda(e);
 }
 
 int default_rpw(int32_t n, int64_t nnz)
@@ -66,7 +89,7 @@ struct sptrsv_plan_st {
     sptrsv_handle h = nullptr;
     bool batched = false;
     sptrsv_dtype dtype = SPTRSV_F64;
-    long long spin = kDefaultSpin;
+    long long spin = kDefaultWaitNs;  // bounded-wait limit, nanoseconds
     int32_t withhold = -1;
     bool have_csc = false;
     std::vector<void *> owned;
@@ -82,6 +105,7 @@ struct sptrsv_plan_st {
     std::vector<PlanMat> mats;
     std::vector<int64_t> rhs_off, vals_off, row_off;
     BatchMat *d_mats = nullptr;
+    std::vector<BatchMat> h_mats;
     int32_t *d_order = nullptr;
     int64_t *d_row_off = nullptr;
     size_t batch_smem = 0;
@@ -361,7 +385,7 @@ sptrsv_status solve_impl(sptrsv_plan p, const void *b, void *x, int32_t nrhs, in
         e = solve_syncfree<T>(A, R, p->rpw, kt, trans, sy, p->grid_sf, s);
         break;
     }
-    return from_cuda(e);
+    return debug_sync(from_cuda(e), s, trans ? "solve_transpose" : "solve");
 }
 
 }  // namespace
@@ -391,7 +415,7 @@ extern "C" sptrsv_status sptrsv_analyze(sptrsv_handle h, const sptrsv_csr *L, in
         return from_cuda(cudaStreamSynchronize(h->stream));
     }
     double tmp[6];
-    return analyze_into(h, *L, lev, perm, level_ptr, level_cost, nlevels, stats ? stats : tmp, kDefaultSpin);
+    return analyze_into(h, *L, lev, perm, level_ptr, level_cost, nlevels, stats ? stats : tmp, kDefaultWaitNs);
 }
 
 // ---------------------------------------------------------------- rewrite
@@ -423,7 +447,7 @@ extern "C" sptrsv_status sptrsv_plan_create(sptrsv_handle h, const sptrsv_csr *L
     p->dtype = L->dtype;
     sptrsv_plan_opts o{};
     if (opts) o = *opts;
-    if (o.spin_limit > 0) p->spin = o.spin_limit;
+    if (o.wait_limit_us > 0) p->spin = o.wait_limit_us * 1000;
     cudaError_t e = p->alloc(&p->d_ctl, sizeof(PlanCtl));
     if (e == cudaSuccess) e = cudaMemset(p->d_ctl, 0, sizeof(PlanCtl));
     if (e == cudaSuccess) e = p->alloc(&p->d_flags, sizeof(uint32_t) * (size_t)(L->n > 0 ? L->n : 1));
@@ -550,7 +574,7 @@ extern "C" sptrsv_status sptrsv_batch_plan_create(sptrsv_handle h, int32_t nmat,
     p->have_csc = false;
     bool want_csc = false;
     for (int m = 0; m < nmat && opts; ++m) want_csc = want_csc || opts[m].build_transpose;
-    if (opts && opts[0].spin_limit > 0) p->spin = opts[0].spin_limit;
+    if (opts && opts[0].wait_limit_us > 0) p->spin = opts[0].wait_limit_us * 1000;
     cudaError_t e = p->alloc(&p->d_ctl, sizeof(PlanCtl));
     if (e == cudaSuccess) e = cudaMemset(p->d_ctl, 0, sizeof(PlanCtl));
     if (e != cudaSuccess) { sptrsv_plan_destroy(p); return from_cuda(e); }
@@ -606,7 +630,32 @@ extern "C" sptrsv_status sptrsv_batch_plan_create(sptrsv_handle h, int32_t nmat,
     if (e != cudaSuccess || smem > kBlockSmemBudget) { sptrsv_plan_destroy(p); return e != cudaSuccess ? from_cuda(e) : SPTRSV_ENOTSUP; }
     p->batch_smem = smem;
     p->batch_grid_sz = std::min(batch_grid(smem, h->di), std::max(nmat, 1));
+    p->h_mats = hm;
     *plan = p;
+    return SPTRSV_OK;
+}
+
+extern "C" sptrsv_status sptrsv_batch_plan_set(sptrsv_plan p, const int32_t *rows_per_warp)
+{
+    if (!p || !p->batched || !rows_per_warp) return SPTRSV_EINVAL;
+    const int32_t nmat = (int32_t)p->h_mats.size();
+    const bool f64 = p->dtype == SPTRSV_F64;
+    for (int m = 0; m < nmat; ++m)
+        if (rows_per_warp[m] != 0 && !valid_rpw(rows_per_warp[m])) return SPTRSV_EINVAL;
+    size_t smem = 16;
+    for (int m = 0; m < nmat; ++m) {
+        BatchMat &B = p->h_mats[m];
+        if (rows_per_warp[m]) B.rpw = rows_per_warp[m];
+        block_geometry(B.rpw, B.kt, f64, &B.kc, &B.P);
+        smem = std::max(smem, block_smem_bytes(B.rpw, B.kt, B.kc, f64));
+    }
+    if (smem > kBlockSmemBudget) return SPTRSV_ENOTSUP;
+    cudaError_t e = cudaStreamSynchronize(p->h->stream);
+    if (e == cudaSuccess && nmat > 0)
+        e = cudaMemcpy(p->d_mats, p->h_mats.data(), sizeof(BatchMat) * nmat, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return from_cuda(e);
+    p->batch_smem = smem;
+    p->batch_grid_sz = std::min(batch_grid(smem, p->h->di), std::max(nmat, 1));
     return SPTRSV_OK;
 }
 
@@ -634,7 +683,7 @@ sptrsv_status batch_solve_impl(sptrsv_plan p, const void *b, void *x, bool trans
     else
         e = batch_solve<float>(p->d_mats, nmat, p->d_order, (const float *)b, (float *)x, trans, p->d_ctl, w,
                                p->batch_grid_sz, p->batch_smem, p->h->stream);
-    return from_cuda(e);
+    return debug_sync(from_cuda(e), p->h->stream, "batch_solve");
 }
 }  // namespace
 

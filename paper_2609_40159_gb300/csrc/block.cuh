@@ -37,7 +37,6 @@ __device__ bool block_solve(const Sys<T> &A, const Rhs<T> &R, int rpw, int kc, i
     const int n = A.n;
     const int ring = kc * rpw;
     const int nchunks = (n + rpw - 1) / rpw;
-    const long long slimit = w.limit * 16;
     for (;;) {
         int c = 0;
         if (lane == 0) c = atomicAdd(sm.ctr, 1);
@@ -45,12 +44,9 @@ __device__ bool block_solve(const Sys<T> &A, const Rhs<T> &R, int rpw, int kc, i
         if (c >= nchunks) return true;
         int ok = 1;
         if (lane == 0 && c - P >= 0) {
-            long long polls = 0;
+            WaitClock clk;
             while (*(volatile int *)(sm.ctr + 1) <= c - P) {
-                if ((++polls & 1023) == 0) {
-                    if (aborted(w)) { ok = 0; break; }
-                    if (polls >= slimit) { give_up(w); ok = 0; break; }
-                }
+                if (clk.expired(w)) { ok = 0; break; }
             }
         }
         ok = __shfl_sync(SPT_FULL_MASK, ok, 0);
@@ -103,12 +99,9 @@ __device__ bool block_solve(const Sys<T> &A, const Rhs<T> &R, int rpw, int kc, i
                     } else {
                         const int slot = pj % ring;
                         if (sm.tag[slot] != pj) {
-                            long long polls = 0;
+                            WaitClock clk;
                             while (sm.tag[slot] != pj) {
-                                if ((++polls & 1023) == 0) {
-                                    if (aborted(w)) { failed = true; break; }
-                                    if (polls >= slimit) { give_up(w); failed = true; break; }
-                                }
+                                if (clk.expired(w)) { failed = true; break; }
                             }
                             if (failed) break;
                         }

@@ -56,14 +56,22 @@ __device__ __forceinline__ void red_release_add(unsigned long long *p, unsigned 
 template <class T> __device__ __forceinline__ T ldro(const T *p) { return __ldg(p); }
 
 // ------------------------------------------------------------- bounded waits
-// Every spin in this library gives up after `limit` polls: it records
-// SPTRSV_ETIMEOUT, raises the shared abort flag and returns false, so that all
-// other waiters also leave instead of spinning on work that will never come.
+// Every wait in this library is bounded in time (%globaltimer, nanoseconds):
+// after `limit_ns` it records SPTRSV_ETIMEOUT, raises the shared abort flag
+// and returns false, so that all other waiters also leave instead of
+// spinning on work that will never come.
 struct Waiter {
     int *status;
     int *abort_flag;
-    long long limit;
+    long long limit_ns;
 };
+
+__device__ __forceinline__ unsigned long long now_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 
 __device__ __forceinline__ bool aborted(const Waiter &w)
 {
@@ -76,17 +84,29 @@ __device__ __forceinline__ void give_up(const Waiter &w)
     st_relaxed(w.abort_flag, 1);
 }
 
+// Checked every 256 polls: abort raised elsewhere, or this wait out of time.
+struct WaitClock {
+    unsigned long long start = 0;
+    unsigned polls = 0;
+    __device__ __forceinline__ bool expired(const Waiter &w)
+    {
+        if ((++polls & 255u) != 0) return false;
+        if (aborted(w)) return true;
+        const unsigned long long t = now_ns();
+        if (start == 0) { start = t; return false; }
+        if ((long long)(t - start) > w.limit_ns) { give_up(w); return true; }
+        return false;
+    }
+};
+
 // Wait until flag == want.  Returns false on timeout / abort.
 __device__ __forceinline__ bool wait_flag(const uint32_t *flag, uint32_t want, const Waiter &w)
 {
     if (ld_acquire(flag) == want) return true;
-    long long polls = 0;
+    WaitClock clk;
     for (;;) {
         if (ld_acquire(flag) == want) return true;
-        if ((++polls & 255) == 0) {
-            if (aborted(w)) return false;
-            if (polls >= w.limit) { give_up(w); return false; }
-        }
+        if (clk.expired(w)) return false;
     }
 }
 
@@ -95,13 +115,10 @@ __device__ __forceinline__ bool wait_count(const unsigned long long *counter,
                                            unsigned long long target, const Waiter &w)
 {
     if (ld_acquire_u64(counter) >= target) return true;
-    long long polls = 0;
+    WaitClock clk;
     for (;;) {
         if (ld_acquire_u64(counter) >= target) return true;
-        if ((++polls & 255) == 0) {
-            if (aborted(w)) return false;
-            if (polls >= w.limit) { give_up(w); return false; }
-        }
+        if (clk.expired(w)) return false;
     }
 }
 

@@ -461,8 +461,13 @@ cudaError_t solve_syncfree(const Sys<T> &A, const Rhs<T> &R, int rpw, int kt, bo
 
 void block_geometry(int rpw, int kt, bool f64, int *kc, int *P)
 {
+    // Throttle distance P (row groups a group may run ahead of the completed
+    // prefix) defaults to the number of warps plus two; the ring holds
+    // kc = 2P groups.  When that does not fit the shared-memory budget
+    // (many right-hand sides), P shrinks; correctness only needs kc >= 2P.
     const int warps = kBlockThreads / 32;
     *P = warps + 2;
+    while (*P > 2 && block_smem_bytes(rpw, kt, 2 * (*P), f64) > kBlockSmemBudget) --(*P);
     *kc = 2 * (*P);
     while (*kc < 4096 / rpw && block_smem_bytes(rpw, kt, (*kc) * 2, f64) <= kBlockSmemBudget / 2)
         *kc *= 2;  // a longer ring keeps more dependencies in shared memory
@@ -470,11 +475,11 @@ void block_geometry(int rpw, int kt, bool f64, int *kc, int *P)
 
 // The dynamic shared-memory limit is raised once per kernel instantiation
 // (outside any stream capture: plans run a first solve before capturing).
-template <class K> static void raise_smem_once(K kernel)
+template <auto Kernel> static void raise_smem_once()
 {
-    static bool done = false;
+    static bool done = false;  // one flag per kernel instantiation
     if (!done) {
-        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBlockSmemBudget);
+        cudaFuncSetAttribute(Kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBlockSmemBudget);
         done = true;
     }
 }
@@ -488,10 +493,10 @@ static cudaError_t blk_launch(const Sys<T> &A, const Rhs<T> &R, int rpw, bool tr
     const size_t smem = block_smem_bytes(rpw, KT, kc, sizeof(T) == 8);
     if (smem > kBlockSmemBudget) return cudaErrorInvalidConfiguration;
     if (trans) {
-        raise_smem_once(k_block<T, KT, true>);
+        raise_smem_once<k_block<T, KT, true>>();
         k_block<T, KT, true><<<1, kBlockThreads, smem, s>>>(A, R, rpw, kc, P, sy);
     } else {
-        raise_smem_once(k_block<T, KT, false>);
+        raise_smem_once<k_block<T, KT, false>>();
         k_block<T, KT, false><<<1, kBlockThreads, smem, s>>>(A, R, rpw, kc, P, sy);
     }
     return cudaGetLastError();
@@ -509,8 +514,6 @@ bool block_mode_supported(int k, bool f64)
     if (k < 1 || k > 32) return false;
     const int kt = block_kt_for(k);
     int kc, P;
-    block_geometry(1, kt, f64, &kc, &P);
-    if (block_smem_bytes(1, kt, kc, f64) > kBlockSmemBudget) return false;
     block_geometry(32, kt, f64, &kc, &P);
     return block_smem_bytes(32, kt, kc, f64) <= kBlockSmemBudget;
 }

@@ -35,6 +35,7 @@ __all__ = [
     "diagonal",
     "rhs",
     "batch_spec",
+    "batch_spec_parallel",
     "BatchItem",
     "narrowest_levels_list",
     "small_levels_list",
@@ -139,14 +140,22 @@ def _window_subsets(rng, n, k, lo, m):
             valid = np.arange(K)[None, :] < kp[:, None]
             SENT = np.iinfo(np.int64).max
             R[~valid] = SENT
-            while True:
-                R.sort(axis=1)
-                dup = np.zeros(R.shape, dtype=bool)
-                dup[:, 1:] = (R[:, 1:] == R[:, :-1]) & (R[:, 1:] != SENT)
-                if not dup.any():
-                    break
+            R.sort(axis=1)
+            dup = np.zeros(R.shape, dtype=bool)
+            dup[:, 1:] = (R[:, 1:] == R[:, :-1]) & (R[:, 1:] != SENT)
+            active = np.nonzero(dup.any(axis=1))[0]
+            dup = dup[active]
+            while len(active):
+                # redraw the duplicates of the rows that still hold some
+                sub = R[active]
                 rr, cc = np.nonzero(dup)
-                R[rr, cc] = np.floor(rng.random(len(rr)) * mp[rr]).astype(np.int64)
+                sub[rr, cc] = np.floor(rng.random(len(rr)) * mp[active[rr]]).astype(np.int64)
+                sub.sort(axis=1)
+                dup = np.zeros(sub.shape, dtype=bool)
+                dup[:, 1:] = (sub[:, 1:] == sub[:, :-1]) & (sub[:, 1:] != SENT)
+                R[active] = sub
+                keep = dup.any(axis=1)
+                active, dup = active[keep], dup[keep]
             R = R + lp[:, None]
             flat = R[valid]  # row-major: the first k[r] (ascending) of each row
             within = np.arange(int(kp.sum())) - np.repeat(np.cumsum(kp) - kp, kp)
@@ -330,16 +339,36 @@ def batch_spec(nmat: int = 512, seed: int = 3, n_lo: int = 1000, n_hi: int = 200
     odd-indexed matrices are marked for a pre-applied rewrite.
     """
     children = np.random.SeedSequence(seed).spawn(nmat)
-    out = []
-    for m, ss in enumerate(children):
-        rng = np.random.default_rng(ss)
-        n = int(round(math.exp(rng.uniform(math.log(n_lo), math.log(n_hi)))))
-        w = int(round(math.exp(rng.uniform(math.log(w_lo), math.log(w_hi)))))
-        k = int(round(math.exp(rng.uniform(0.0, math.log(32.0)))))
-        A = band_random(n, w, 4, 16, rng=rng, dtype=dtype)
-        b = rhs(n, k, rng=rng, dtype=dtype) if with_rhs else None
-        out.append(BatchItem(A, k, w, b, rewritten=(m % 2 == 1)))
-    return out
+    return [_batch_one((m, ss, n_lo, n_hi, w_lo, w_hi, dtype, with_rhs))
+            for m, ss in enumerate(children)]
+
+
+def _batch_one(args):
+    m, ss, n_lo, n_hi, w_lo, w_hi, dtype, with_rhs = args
+    rng = np.random.default_rng(ss)
+    n = int(round(math.exp(rng.uniform(math.log(n_lo), math.log(n_hi)))))
+    w = int(round(math.exp(rng.uniform(math.log(w_lo), math.log(w_hi)))))
+    k = int(round(math.exp(rng.uniform(0.0, math.log(32.0)))))
+    A = band_random(n, w, 4, 16, rng=rng, dtype=dtype)
+    b = rhs(n, k, rng=rng, dtype=dtype) if with_rhs else None
+    return BatchItem(A, k, w, b, rewritten=(m % 2 == 1))
+
+
+def batch_spec_parallel(nmat: int = 512, seed: int = 3, workers: int | None = None, **kw):
+    """``batch_spec`` computed by a pool of worker processes (spawned, so it
+    is safe after CUDA has been initialised); identical output, since every
+    system draws from its own child seed."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    import os
+    n_lo, n_hi = kw.get("n_lo", 1000), kw.get("n_hi", 200_000)
+    w_lo, w_hi = kw.get("w_lo", 16), kw.get("w_hi", 1024)
+    dtype, with_rhs = kw.get("dtype", np.float32), kw.get("with_rhs", True)
+    children = np.random.SeedSequence(seed).spawn(nmat)
+    jobs = [(m, ss, n_lo, n_hi, w_lo, w_hi, dtype, with_rhs) for m, ss in enumerate(children)]
+    workers = workers or min(32, os.cpu_count() or 4)
+    with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+        return list(ex.map(_batch_one, jobs, chunksize=4))
 
 
 # ----------------------------------------------------------------------------

@@ -50,9 +50,11 @@ def test_solve_all_modes(name, dt):
                         continue
                     plan.set(mode, rpw, kt)
                     x = plan.solve(b)
+                    assert P.handle().status() == 0, (mode, rpw, kt, k)
                     e = relerr(x.cpu().numpy(), x_ref)
                     assert e <= TOL[dt], (mode, rpw, kt, k, e)
                     g = plan.solve_transpose(b)
+                    assert P.handle().status() == 0, ("T", mode, rpw, kt, k)
                     e = relerr(g.cpu().numpy(), g_ref)
                     assert e <= TOL[dt], ("T", mode, rpw, kt, k, e)
         assert P.handle().status() == 0
@@ -195,7 +197,7 @@ def test_bounded_wait_reports_timeout(mode):
     A_h = S.chain(5000, seed=1)
     A = P.Matrix.from_host(A_h)
     b = torch.as_tensor(S.rhs(A_h.n, 1, seed=1)).cuda()
-    plan = P.Plan(A, mode=mode, spin_limit=1 << 12)
+    plan = P.Plan(A, mode=mode, rows_per_warp=1, wait_limit_us=20_000)
     h = P.handle()
     assert h.status() == 0
     plan.withhold(100)      # row 100's ready flag is never released
