@@ -217,6 +217,32 @@ sptrsv_status sptrsv_batch_grad_vals(sptrsv_plan plan, const void *gb, const voi
                                      void *gvals);
 sptrsv_status sptrsv_batch_tt_apply(sptrsv_plan plan, const void *gbp, void *gb);
 
+/* --------------------------------------------------- allocation-free solve */
+/* The paper has no counterpart of this entry point; it exists for callers
+ * that cannot allocate device memory when they solve (an application whose
+ * own pool owns the device memory budget, a real-time loop that cannot take
+ * cudaMalloc's implicit synchronisation, a plug-in whose host forbids
+ * allocation).  It needs no handle and no plan: x = L^{-1} b by the
+ * synchronisation-free forward solve, with its scratch (one ready flag per
+ * row plus a control block) in a static device array of this library,
+ * sized for at most SPTRSV_NOALLOC_MAX_ROWS rows (4 MiB, held on every
+ * device that loads the library until the process exits).
+ *   L       matrix descriptor (device arrays, not validated here: validate
+ *           it once with sptrsv_validate);
+ *   b, x    [n x nrhs] row-major with leading dimension ld (device);
+ *   stream  cudaStream_t to run on (NULL = legacy default stream).
+ * Returns SPTRSV_ENOTSUP when n > SPTRSV_NOALLOC_MAX_ROWS (nothing is
+ * launched), SPTRSV_EINVAL for bad arguments, SPTRSV_ETIMEOUT when a bounded
+ * wait gave up, SPTRSV_ECUDA for a CUDA failure.  Synchronises the stream
+ * before returning.  The first call on a device looks up the device address
+ * of the scratch array (and may load the library's GPU code): make it before
+ * any stream capture.  All calls on a device share the one scratch array,
+ * so calls that overlap on the GPU (other streams, other host threads) race
+ * and must be serialised by the caller.  Calls no cudaMalloc / cudaFree.     */
+#define SPTRSV_NOALLOC_MAX_ROWS (1 << 20)
+sptrsv_status sptrsv_solve_noalloc(const sptrsv_csr *L, const void *b, void *x, int32_t nrhs,
+                                   int64_t ld, void *stream);
+
 /* ------------------------------------------------------------- diagnostics */
 /* Test hook for the bounded waits: makes the next solves of `plan` skip
  * publishing row `row` (-1 clears it), so that any row waiting on it gives

@@ -14,7 +14,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsptrsv_gb300.so")
-SOURCES = ["api.cu", "analyze.cu", "prims.cu", "rewrite.cu", "solve.cu", "batch.cu"]
+SOURCES = ["api.cu", "analyze.cu", "prims.cu", "rewrite.cu", "solve.cu", "batch.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
 
