@@ -244,6 +244,12 @@ sptrsv_status sptrsv_solve_noalloc(const sptrsv_csr *L, const void *b, void *x, 
                                    int64_t ld, void *stream);
 
 /* ------------------------------------------------------------- diagnostics */
+/* Trace of the last batched solve of `plan`: for every system m,
+ * trace[3m] and trace[3m+1] are the GPU global-timer values (ns) when a
+ * thread block started and finished it, trace[3m+2] the SM it ran on
+ * (host array of 3*nmat entries).  Synchronises.                            */
+sptrsv_status sptrsv_batch_trace(sptrsv_plan plan, int64_t *trace);
+
 /* Test hook for the bounded waits: makes the next solves of `plan` skip
  * publishing row `row` (-1 clears it), so that any row waiting on it gives
  * up after wait_limit_us and the solve reports SPTRSV_ETIMEOUT.            */

@@ -309,6 +309,14 @@ class BatchPlan:
         L.check(L.lib().sptrsv_batch_tt_apply(self.p, _ptr(gbp), _ptr(gb)), "sptrsv_batch_tt_apply")
         return gb
 
+    def trace(self):
+        """[nmat, 3] int64: start ns, end ns, SM of every system in the last
+        batched solve."""
+        nmat = len(self.mats)
+        buf = (C.c_int64 * (3 * max(nmat, 1)))()
+        L.check(L.lib().sptrsv_batch_trace(self.p, buf), "sptrsv_batch_trace")
+        return np.array(list(buf), dtype=np.int64)[: 3 * nmat].reshape(nmat, 3)
+
     def unpack(self, packed, m):
         a, b = int(self.rhs_offset[m]), int(self.rhs_offset[m + 1])
         return packed[a:b].view(self.mats[m].n, self.nrhs[m])

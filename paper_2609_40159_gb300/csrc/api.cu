@@ -101,6 +101,7 @@ struct sptrsv_plan_st {
     int chunk_rpw = 0;
     uint32_t *d_flags = nullptr;
     int grid_level = 0, grid_sf = 0;
+    int32_t max_width = 0;
     // batched
     std::vector<PlanMat> mats;
     std::vector<int64_t> rhs_off, vals_off, row_off;
@@ -108,6 +109,7 @@ struct sptrsv_plan_st {
     std::vector<BatchMat> h_mats;
     int32_t *d_order = nullptr;
     int64_t *d_row_off = nullptr;
+    long long *d_trace = nullptr;  // per system: start ns, end ns, SM of the last batch solve
     size_t batch_smem = 0;
     int batch_grid_sz = 0;
 
@@ -375,12 +377,16 @@ sptrsv_status solve_impl(sptrsv_plan p, const void *b, void *x, int32_t nrhs, in
         if (st != SPTRSV_OK) return st;
         Sched S{M.d_perm, M.d_level_ptr, M.nlevels, trans ? p->d_chunk_tr : p->d_chunk_fwd,
                 ((int64_t)M.L.n + p->rpw - 1) / p->rpw};
-        e = solve_level_persistent<T>(A, S, R, p->rpw, kt, trans, sy, p->grid_level, s);
+        const int64_t want = (2 * (int64_t)p->max_width / p->rpw + 7) / 8;  // blocks of 8 warps
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(p->grid_level, want));
+        e = solve_level_persistent<T>(A, S, R, p->rpw, kt, trans, sy, grid, s);
         break;
     }
-    case SPTRSV_MODE_BLOCK:
-        e = solve_block<T>(A, R, p->rpw, kt, trans, sy, s);
+    case SPTRSV_MODE_BLOCK: {
+        const double width = M.nlevels > 0 ? (double)M.L.n / M.nlevels : 1.0;
+        e = solve_block<T>(A, R, p->rpw, kt, trans, sy, block_warps_for(width, p->rpw), s);
         break;
+    }
     default:
         e = solve_syncfree<T>(A, R, p->rpw, kt, trans, sy, p->grid_sf, s);
         break;
@@ -461,6 +467,14 @@ extern "C" sptrsv_status sptrsv_plan_create(sptrsv_handle h, const sptrsv_csr *L
     p->kt = valid_kt(o.rhs_tile) ? o.rhs_tile : 16;
     if (p->mode < SPTRSV_MODE_LEVEL_LAUNCH || p->mode > SPTRSV_MODE_BLOCK) { sptrsv_plan_destroy(p); return SPTRSV_EINVAL; }
     p->grid_level = persistent_grid_level(1, p->dtype == SPTRSV_F64, h->di);
+    {
+        // warps beyond about twice the widest level only poll the progress
+        // counter: cap the level-persistent grid accordingly
+        int32_t maxw = 0;
+        for (int32_t l = 0; l < p->M.nlevels; ++l)
+            maxw = std::max(maxw, p->M.h_level_ptr[l + 1] - p->M.h_level_ptr[l]);
+        p->max_width = maxw;
+    }
     p->grid_sf = persistent_grid_syncfree(1, p->dtype == SPTRSV_F64, h->di);
     st = ensure_chunks(p);
     if (st == SPTRSV_OK) st = from_cuda(cudaStreamSynchronize(h->stream));
@@ -599,8 +613,9 @@ extern "C" sptrsv_status sptrsv_batch_plan_create(sptrsv_handle h, int32_t nmat,
         const int orpw = opts ? opts[m].rows_per_warp : 0;
         B.rpw = valid_rpw(orpw) ? orpw : default_rpw(M.L.n, M.L.nnz);
         B.kt = block_kt_for(B.k);
-        block_geometry(B.rpw, B.kt, f64, &B.kc, &B.P);
-        smem = std::max(smem, block_smem_bytes(B.rpw, B.kt, B.kc, f64));
+        B.nw = block_warps_for(M.nlevels > 0 ? (double)M.L.n / M.nlevels : 1.0, B.rpw);
+        block_geometry(B.rpw, B.kt, f64, B.nw, &B.kc, &B.P);
+        smem = std::max(smem, block_smem_bytes(B.rpw, B.kt, B.kc, f64, B.nw));
         B.nnz = M.L.nnz;
         B.rp = M.L.row_ptr; B.ci = M.L.col_idx; B.v = M.L.vals;
         B.cp = M.d_cp; B.crow = M.d_crow; B.tmap = M.d_tmap;
@@ -624,6 +639,7 @@ extern "C" sptrsv_status sptrsv_batch_plan_create(sptrsv_handle h, int32_t nmat,
     e = p->alloc(&p->d_mats, sizeof(BatchMat) * (size_t)(nmat > 0 ? nmat : 1));
     if (e == cudaSuccess) e = p->alloc(&p->d_order, sizeof(int32_t) * (size_t)(nmat > 0 ? nmat : 1));
     if (e == cudaSuccess) e = p->alloc(&p->d_row_off, sizeof(int64_t) * ((size_t)nmat + 1));
+    if (e == cudaSuccess) e = p->alloc(&p->d_trace, sizeof(long long) * 3 * (size_t)(nmat > 0 ? nmat : 1));
     if (e == cudaSuccess && nmat > 0) e = cudaMemcpy(p->d_mats, hm.data(), sizeof(BatchMat) * nmat, cudaMemcpyHostToDevice);
     if (e == cudaSuccess && nmat > 0) e = cudaMemcpy(p->d_order, order.data(), sizeof(int32_t) * nmat, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(p->d_row_off, p->row_off.data(), sizeof(int64_t) * (nmat + 1), cudaMemcpyHostToDevice);
@@ -646,8 +662,10 @@ extern "C" sptrsv_status sptrsv_batch_plan_set(sptrsv_plan p, const int32_t *row
     for (int m = 0; m < nmat; ++m) {
         BatchMat &B = p->h_mats[m];
         if (rows_per_warp[m]) B.rpw = rows_per_warp[m];
-        block_geometry(B.rpw, B.kt, f64, &B.kc, &B.P);
-        smem = std::max(smem, block_smem_bytes(B.rpw, B.kt, B.kc, f64));
+        const PlanMat &M = p->mats[m];
+        B.nw = block_warps_for(M.nlevels > 0 ? (double)M.L.n / M.nlevels : 1.0, B.rpw);
+        block_geometry(B.rpw, B.kt, f64, B.nw, &B.kc, &B.P);
+        smem = std::max(smem, block_smem_bytes(B.rpw, B.kt, B.kc, f64, B.nw));
     }
     if (smem > kBlockSmemBudget) return SPTRSV_ENOTSUP;
     cudaError_t e = cudaStreamSynchronize(p->h->stream);
@@ -679,10 +697,10 @@ sptrsv_status batch_solve_impl(sptrsv_plan p, const void *b, void *x, bool trans
     cudaError_t e;
     if (p->dtype == SPTRSV_F64)
         e = batch_solve<double>(p->d_mats, nmat, p->d_order, (const double *)b, (double *)x, trans, p->d_ctl, w,
-                                p->batch_grid_sz, p->batch_smem, p->h->stream);
+                                p->batch_grid_sz, p->batch_smem, p->d_trace, p->h->stream);
     else
         e = batch_solve<float>(p->d_mats, nmat, p->d_order, (const float *)b, (float *)x, trans, p->d_ctl, w,
-                               p->batch_grid_sz, p->batch_smem, p->h->stream);
+                               p->batch_grid_sz, p->batch_smem, p->d_trace, p->h->stream);
     return debug_sync(from_cuda(e), p->h->stream, "batch_solve");
 }
 }  // namespace
@@ -695,6 +713,17 @@ extern "C" sptrsv_status sptrsv_batch_solve(sptrsv_plan p, const void *b, void *
 extern "C" sptrsv_status sptrsv_batch_solve_transpose(sptrsv_plan p, const void *gx, void *gb)
 {
     return batch_solve_impl(p, gx, gb, true);
+}
+
+extern "C" sptrsv_status sptrsv_batch_trace(sptrsv_plan p, int64_t *trace)
+{
+    if (!p || !p->batched || !trace) return SPTRSV_EINVAL;
+    const size_t nmat = p->mats.size();
+    if (nmat == 0) return SPTRSV_OK;
+    cudaError_t e = cudaStreamSynchronize(p->h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(trace, p->d_trace, sizeof(long long) * 3 * nmat, cudaMemcpyDeviceToHost);
+    return from_cuda(e);
 }
 
 extern "C" sptrsv_status sptrsv_batch_grad_vals(sptrsv_plan p, const void *gb, const void *x, void *gvals)

@@ -27,7 +27,7 @@ __device__ __forceinline__ bool run_one(const BatchMat &M, unsigned char *raw, c
                                         const Waiter &w)
 {
     const int ring = M.kc * M.rpw;
-    BlockSmem<T, KT> sm = carve_block_smem<T, KT>(raw, ring, M.kc);
+    BlockSmem<T, KT> sm = carve_block_smem<T, KT>(raw, ring, M.kc, M.nw);
     reset_block_smem<T, KT>(sm, ring, M.kc);
     __syncthreads();
     Rhs<T> R;
@@ -35,13 +35,20 @@ __device__ __forceinline__ bool run_one(const BatchMat &M, unsigned char *raw, c
     R.x = x + M.rhs_off;
     R.ld = M.k;
     R.k = M.k;
-    return block_solve<T, KT, TR>(sys_of<T>(M), R, M.rpw, M.kc, M.P, sm, w, -1);
+    return block_solve_any<T, KT, TR>(sys_of<T>(M), R, M.rpw, M.kc, M.P, M.nw, sm, w, -1);
+}
+
+__device__ __forceinline__ unsigned sm_id()
+{
+    unsigned r;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(r));
+    return r;
 }
 
 template <class T, bool TR>
 __global__ void __launch_bounds__(kBatchThreads)
 k_batch(const BatchMat *__restrict__ mats, int32_t nmat, const int32_t *__restrict__ order,
-        const T *b, T *x, PlanCtl *ctl, Waiter w)
+        const T *b, T *x, PlanCtl *ctl, Waiter w, long long *trace)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ int s_next, s_stop;
@@ -55,7 +62,12 @@ k_batch(const BatchMat *__restrict__ mats, int32_t nmat, const int32_t *__restri
         const int stop = s_stop;
         __syncthreads();
         if (t >= nmat || stop) return;
-        const BatchMat M = mats[order[t]];
+        const int m = order[t];
+        const BatchMat M = mats[m];
+        if (trace && threadIdx.x == 0) {
+            trace[3 * m] = (long long)now_ns();
+            trace[3 * m + 2] = (long long)sm_id();
+        }
         switch (M.kt) {
         case 1: run_one<T, 1, TR>(M, smraw, b, x, w); break;
         case 2: run_one<T, 2, TR>(M, smraw, b, x, w); break;
@@ -65,6 +77,7 @@ k_batch(const BatchMat *__restrict__ mats, int32_t nmat, const int32_t *__restri
         default: run_one<T, 32, TR>(M, smraw, b, x, w); break;
         }
         __syncthreads();
+        if (trace && threadIdx.x == 0) trace[3 * m + 1] = (long long)now_ns();
     }
 }
 
@@ -153,14 +166,14 @@ int batch_grid(size_t smem, const DeviceInfo &di)
 template <class T>
 cudaError_t batch_solve(const BatchMat *mats, int32_t nmat, const int32_t *order, const T *b,
                         T *x, bool trans, PlanCtl *ctl, const Waiter &w, int grid,
-                        size_t smem, cudaStream_t s)
+                        size_t smem, long long *trace, cudaStream_t s)
 {
     cudaError_t e = launch_prologue<T>(ctl, s);
     if (e != cudaSuccess || nmat <= 0) return e;
     if (trans) {
-        k_batch<T, true><<<grid, kBatchThreads, smem, s>>>(mats, nmat, order, b, x, ctl, w);
+        k_batch<T, true><<<grid, kBatchThreads, smem, s>>>(mats, nmat, order, b, x, ctl, w, trace);
     } else {
-        k_batch<T, false><<<grid, kBatchThreads, smem, s>>>(mats, nmat, order, b, x, ctl, w);
+        k_batch<T, false><<<grid, kBatchThreads, smem, s>>>(mats, nmat, order, b, x, ctl, w, trace);
     }
     return cudaGetLastError();
 }
@@ -192,7 +205,7 @@ cudaError_t batch_tt_apply(const BatchMat *mats, int32_t nmat, const int64_t *ro
 #define SPT_INST(T)                                                                              \
     template cudaError_t batch_solve<T>(const BatchMat *, int32_t, const int32_t *, const T *, T *, \
                                         bool, PlanCtl *, const Waiter &, int, size_t,            \
-                                        cudaStream_t);                                           \
+                                        long long *, cudaStream_t);                              \
     template cudaError_t batch_grad_vals<T>(const BatchMat *, int32_t, const int64_t *, int64_t, \
                                             const T *, const T *, T *, cudaStream_t);            \
     template cudaError_t batch_tt_apply<T>(const BatchMat *, int32_t, const int64_t *, int64_t,  \

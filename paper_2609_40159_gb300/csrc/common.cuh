@@ -52,6 +52,20 @@ __device__ __forceinline__ void red_release_add(unsigned long long *p, unsigned 
     asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
+// CTA-scope release/acquire on shared memory (ring tags of the block mode).
+__device__ __forceinline__ int ld_acquire_cta_smem(const int *p)
+{
+    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+    int v;
+    asm volatile("ld.acquire.cta.shared.s32 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_cta_smem(int *p, int v)
+{
+    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+    asm volatile("st.release.cta.shared.s32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+
 // Read-only (for the whole kernel) matrix data: non-coherent path.
 template <class T> __device__ __forceinline__ T ldro(const T *p) { return __ldg(p); }
 
@@ -84,18 +98,35 @@ __device__ __forceinline__ void give_up(const Waiter &w)
     st_relaxed(w.abort_flag, 1);
 }
 
-// Checked every 256 polls: abort raised elsewhere, or this wait out of time.
+// Bounded-wait bookkeeping, cheap enough for tight shared-memory spins: the
+// elapsed time comes from the SM-local clock64 (compared against the limit
+// at 2.2 GHz, at or above the GB300 maximum SM clock, so the wall-time limit
+// is never undercut by much), the global abort flag is read only every
+// 4096 polls.
 struct WaitClock {
-    unsigned long long start = 0;
+    long long start = 0;
     unsigned polls = 0;
     __device__ __forceinline__ bool expired(const Waiter &w)
     {
-        if ((++polls & 255u) != 0) return false;
-        if (aborted(w)) return true;
-        const unsigned long long t = now_ns();
+        ++polls;
+        if ((polls & 63u) != 0) return false;
+        const long long t = clock64();
         if (start == 0) { start = t; return false; }
-        if ((long long)(t - start) > w.limit_ns) { give_up(w); return true; }
+        if ((polls & 4095u) == 0 && aborted(w)) return true;
+        if ((double)(t - start) > 2.2 * (double)w.limit_ns) { give_up(w); return true; }
         return false;
+    }
+};
+
+// Global-memory polls back off exponentially (__nanosleep, 32 ns .. 512 ns)
+// so that thousands of waiting warps do not saturate the L2 slice that holds
+// the flag the producer is about to write.
+struct Backoff {
+    unsigned ns = 32;
+    __device__ __forceinline__ void pause()
+    {
+        __nanosleep(ns);
+        if (ns < 512) ns <<= 1;
     }
 };
 
@@ -104,9 +135,11 @@ __device__ __forceinline__ bool wait_flag(const uint32_t *flag, uint32_t want, c
 {
     if (ld_acquire(flag) == want) return true;
     WaitClock clk;
+    Backoff bo;
     for (;;) {
         if (ld_acquire(flag) == want) return true;
         if (clk.expired(w)) return false;
+        bo.pause();
     }
 }
 
@@ -116,9 +149,11 @@ __device__ __forceinline__ bool wait_count(const unsigned long long *counter,
 {
     if (ld_acquire_u64(counter) >= target) return true;
     WaitClock clk;
+    Backoff bo;
     for (;;) {
         if (ld_acquire_u64(counter) >= target) return true;
         if (clk.expired(w)) return false;
+        bo.pause();
     }
 }
 

@@ -123,16 +123,19 @@ k_level_persistent(Sys<T> A, Sched S, Rhs<T> R, int rpw, SyncArgs sy)
             const int lstart = TR ? n - S.level_ptr[L - l] : S.level_ptr[l];
             const int lend = TR ? n - S.level_ptr[L - 1 - l] : S.level_ptr[l + 1];
             const int lo = max(q0, lstart), hi = min(q1, lend);
-            int ok = 1;
-            if (lane == 0) ok = wait_count(&sy.ctl->progress, (unsigned long long)lstart, sy.w);
-            ok = __shfl_sync(SPT_FULL_MASK, ok, 0);
-            if (!ok) return;
-            __syncwarp();
+            // row metadata and the reciprocal diagonal do not depend on the
+            // solution: load them before waiting for the previous levels
             const int q = q0 + g;
             const bool active = q >= lo && q < hi;
             const int i = active ? (TR ? S.perm[n - 1 - q] : S.perm[q]) : 0;
             const int a = active ? RV<T, TR>::beg(A, i) : 0;
             const int e = active ? RV<T, TR>::end(A, i) : 0;
+            const T rinv = active ? T(1) / RV<T, TR>::diag(A, a, e) : T(0);
+            int ok = 1;
+            if (lane == 0) ok = wait_count(&sy.ctl->progress, (unsigned long long)lstart, sy.w);
+            ok = __shfl_sync(SPT_FULL_MASK, ok, 0);
+            if (!ok) return;
+            __syncwarp();
             for (int r0 = 0; r0 < R.k; r0 += KT) {
                 const int kt = min(KT, R.k - r0);
                 T acc[KT];
@@ -141,12 +144,11 @@ k_level_persistent(Sys<T> A, Sched S, Rhs<T> R, int rpw, SyncArgs sy)
                 if (active) gather_row<T, KT, TR>(A, R, i, a, e, sl, lpr, r0, kt, acc);
                 group_reduce<T, KT>(acc, lpr);
                 if (active && sl == 0) {
-                    const T d = RV<T, TR>::diag(A, a, e);
                     const T *bb = R.b + (int64_t)i * R.ld + r0;
                     T *xx = R.x + (int64_t)i * R.ld + r0;
 #pragma unroll
                     for (int r = 0; r < KT; ++r)
-                        if (r < kt) xx[r] = (bb[r] - acc[r]) / d;
+                        if (r < kt) xx[r] = (bb[r] - acc[r]) * rinv;
                 }
             }
             __syncwarp();
@@ -263,26 +265,125 @@ k_syncfree(Sys<T> A, Rhs<T> R, int rpw, SyncArgs sy)
     }
 }
 
+// Sync-free solve with one lane per row: dependencies on earlier groups are
+// waited for through their ready flags, dependencies inside the group are
+// resolved by the column sweep (lane s's solution broadcast at step s).
+constexpr int kSwThreads = 128;
+constexpr int kSwWarps = kSwThreads / 32;
+
+template <class T, int KT, bool TR>
+__global__ void __launch_bounds__(kSwThreads)
+k_syncfree_sweep(Sys<T> A, Rhs<T> R, SyncArgs sy)
+{
+    __shared__ T coef_all[kSwWarps][1024];
+    __shared__ T xbuf_all[kSwWarps][32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    T *coef = coef_all[wid];
+    T *xbuf = xbuf_all[wid];
+    const int n = A.n;
+    const uint32_t epoch = (uint32_t)sy.ctl->epoch;
+    const int64_t nchunks = ((int64_t)n + 31) / 32;
+    for (;;) {
+        unsigned long long c = 0;
+        if (lane == 0) c = atomicAdd(&sy.ctl->ticket, 1ull);
+        c = __shfl_sync(SPT_FULL_MASK, c, 0);
+        if ((int64_t)c >= nchunks) return;
+        const int base = (int)c * 32;
+        const int pos = base + lane;
+        const bool valid = pos < n;
+        const int i = valid ? (TR ? n - 1 - pos : pos) : 0;
+        int a = 0, e = 0;
+        T rinv = T(0);
+        if (valid) {
+            a = RV<T, TR>::beg(A, i);
+            e = RV<T, TR>::end(A, i);
+            rinv = T(1) / RV<T, TR>::diag(A, a, e);
+        }
+        for (int r0 = 0; r0 < R.k; r0 += KT) {
+            const int ktile = min(KT, R.k - r0);
+            const bool last_tile = r0 + KT >= R.k;
+            T acc[KT], bv[KT];
+#pragma unroll
+            for (int r = 0; r < KT; ++r) {
+                acc[r] = T(0);
+                bv[r] = (valid && r < ktile) ? R.b[(int64_t)i * R.ld + r0 + r] : T(0);
+            }
+            if (!TR && valid && has_trow(A, i)) {
+                for (int p = A.trp[i]; p < A.trp[i + 1]; ++p) {
+                    const T tv = ldro(A.tv + p);
+                    const T *bb = R.b + (int64_t)ldro(A.tci + p) * R.ld + r0;
+#pragma unroll
+                    for (int r = 0; r < KT; ++r)
+                        if (r < ktile) acc[r] -= tv * bb[r];
+                }
+            }
+            // entries loaded kMaxBatch at a time; earlier groups waited for
+            // through their flags and applied, this group's recorded for the
+            // sweep
+            bool failed = false;
+            unsigned dmask = 0;
+            if (valid) {
+                for (int p0 = a; p0 < e && !failed; p0 += kMaxBatch) {
+                    int jj[kMaxBatch];
+                    T vvv[kMaxBatch];
+#pragma unroll
+                    for (int u = 0; u < kMaxBatch; ++u)
+                        if (p0 + u < e) {
+                            jj[u] = RV<T, TR>::col(A, p0 + u);
+                            vvv[u] = RV<T, TR>::val(A, p0 + u);
+                        }
+#pragma unroll
+                    for (int u = 0; u < kMaxBatch; ++u)
+                        if (p0 + u < e && !failed) {
+                            const int j = jj[u];
+                            const int pj = order_pos<TR>(n, j);
+                            if (pj >= base) {
+                                dmask |= 1u << (pj - base);
+                                coef[(pj - base) * 32 + lane] = vvv[u];
+                                continue;
+                            }
+                            if (!wait_flag(sy.flags + j, epoch, sy.w)) { failed = true; continue; }
+                            const T *xx = R.x + (int64_t)j * R.ld + r0;
+#pragma unroll
+                            for (int r = 0; r < KT; ++r)
+                                if (r < ktile) acc[r] += vvv[u] * xx[r];
+                        }
+                }
+            }
+            if (__any_sync(SPT_FULL_MASK, failed)) return;
+            group_sweep<T, KT>(dmask, coef, xbuf, acc, bv, rinv);
+            if (valid) {
+                T *xx = R.x + (int64_t)i * R.ld + r0;
+#pragma unroll
+                for (int r = 0; r < KT; ++r)
+                    if (r < ktile) xx[r] = (bv[r] - acc[r]) * rinv;
+                if (last_tile && i != sy.withhold) st_release(sy.flags + i, epoch);
+            }
+            __syncwarp();
+        }
+    }
+}
+
 constexpr int kBlockThreads = 512;
 
 template <class T, int KT, bool TR>
 __global__ void __launch_bounds__(kBlockThreads)
-k_block(Sys<T> A, Rhs<T> R, int rpw, int kc, int P, SyncArgs sy)
+k_block(Sys<T> A, Rhs<T> R, int rpw, int kc, int P, int nwarps, SyncArgs sy)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
     const int ring = kc * rpw;
-    BlockSmem<T, KT> sm = carve_block_smem<T, KT>(smraw, ring, kc);
+    BlockSmem<T, KT> sm = carve_block_smem<T, KT>(smraw, ring, kc, nwarps);
     reset_block_smem<T, KT>(sm, ring, kc);
     __syncthreads();
-    block_solve<T, KT, TR>(A, R, rpw, kc, P, sm, sy.w, sy.withhold);
+    block_solve_any<T, KT, TR>(A, R, rpw, kc, P, nwarps, sm, sy.w, sy.withhold);
 }
 
-size_t block_smem_bytes(int rpw, int kt, int kc, bool f64)
+size_t block_smem_bytes(int rpw, int kt, int kc, bool f64, int nw)
 {
     const size_t ring = (size_t)kc * rpw;
-    return ring * kt * (f64 ? 8 : 4) + ring * 4 + (size_t)kc * 4 + 16;
+    const size_t w = f64 ? 8 : 4;
+    return ring * kt * w + (size_t)nw * (1024 + 32) * w + ring * 4 + (size_t)kc * 4 + 16;
 }
-
 // ------------------------------------------------------------- gradient
 template <class T>
 __global__ void k_grad_vals(Sys<T> A, const T *__restrict__ gb, const T *__restrict__ x,
@@ -438,6 +539,12 @@ template <class T, int KT>
 static cudaError_t sf_launch(const Sys<T> &A, const Rhs<T> &R, int rpw, bool trans,
                              const SyncArgs &sy, int grid, cudaStream_t s)
 {
+    if (rpw == 32) {
+        // 128-thread blocks: twice as many blocks as the 256-thread grid
+        if (trans) k_syncfree_sweep<T, KT, true><<<2 * grid, kSwThreads, 0, s>>>(A, R, sy);
+        else k_syncfree_sweep<T, KT, false><<<2 * grid, kSwThreads, 0, s>>>(A, R, sy);
+        return cudaGetLastError();
+    }
     if (trans) k_syncfree<T, KT, true><<<grid, kSfThreads, 0, s>>>(A, R, rpw, sy);
     else k_syncfree<T, KT, false><<<grid, kSfThreads, 0, s>>>(A, R, rpw, sy);
     return cudaGetLastError();
@@ -459,18 +566,30 @@ cudaError_t solve_syncfree(const Sys<T> &A, const Rhs<T> &R, int rpw, int kt, bo
 }
 
 
-void block_geometry(int rpw, int kt, bool f64, int *kc, int *P)
+void block_geometry(int rpw, int kt, bool f64, int nwarps, int *kc, int *P)
 {
     // Throttle distance P (row groups a group may run ahead of the completed
-    // prefix) defaults to the number of warps plus two; the ring holds
+    // prefix) defaults to the number of active warps plus two; the ring holds
     // kc = 2P groups.  When that does not fit the shared-memory budget
     // (many right-hand sides), P shrinks; correctness only needs kc >= 2P.
-    const int warps = kBlockThreads / 32;
-    *P = warps + 2;
-    while (*P > 2 && block_smem_bytes(rpw, kt, 2 * (*P), f64) > kBlockSmemBudget) --(*P);
+    *P = nwarps + 2;
+    while (*P > 2 && block_smem_bytes(rpw, kt, 2 * (*P), f64, nwarps) > kBlockSmemBudget) --(*P);
     *kc = 2 * (*P);
-    while (*kc < 4096 / rpw && block_smem_bytes(rpw, kt, (*kc) * 2, f64) <= kBlockSmemBudget / 2)
+    while (*kc < 4096 / rpw && block_smem_bytes(rpw, kt, (*kc) * 2, f64, nwarps) <= kBlockSmemBudget / 2)
         *kc *= 2;  // a longer ring keeps more dependencies in shared memory
+}
+
+int block_warps_for(double rows_per_level, int rpw)
+{
+    // one lane per row (column sweep, groups complete in order): the extra
+    // warps preload later groups, so use all of them
+    if (rpw == 32) return kMaxBlockWarps;
+    // enough row groups in flight to cover about two levels; at least two
+    // warps so that one group's loads overlap the previous group's sweep
+    int w = (int)(2.0 * rows_per_level / rpw + 0.999);
+    if (w < 2) w = 2;
+    if (w > kMaxBlockWarps) w = kMaxBlockWarps;
+    return w;
 }
 
 // The dynamic shared-memory limit is raised once per kernel instantiation
@@ -486,18 +605,18 @@ template <auto Kernel> static void raise_smem_once()
 
 template <class T, int KT>
 static cudaError_t blk_launch(const Sys<T> &A, const Rhs<T> &R, int rpw, bool trans,
-                              const SyncArgs &sy, cudaStream_t s)
+                              const SyncArgs &sy, int nwarps, cudaStream_t s)
 {
     int kc, P;
-    block_geometry(rpw, KT, sizeof(T) == 8, &kc, &P);
-    const size_t smem = block_smem_bytes(rpw, KT, kc, sizeof(T) == 8);
+    block_geometry(rpw, KT, sizeof(T) == 8, nwarps, &kc, &P);
+    const size_t smem = block_smem_bytes(rpw, KT, kc, sizeof(T) == 8, nwarps);
     if (smem > kBlockSmemBudget) return cudaErrorInvalidConfiguration;
     if (trans) {
         raise_smem_once<k_block<T, KT, true>>();
-        k_block<T, KT, true><<<1, kBlockThreads, smem, s>>>(A, R, rpw, kc, P, sy);
+        k_block<T, KT, true><<<1, kBlockThreads, smem, s>>>(A, R, rpw, kc, P, nwarps, sy);
     } else {
         raise_smem_once<k_block<T, KT, false>>();
-        k_block<T, KT, false><<<1, kBlockThreads, smem, s>>>(A, R, rpw, kc, P, sy);
+        k_block<T, KT, false><<<1, kBlockThreads, smem, s>>>(A, R, rpw, kc, P, nwarps, sy);
     }
     return cudaGetLastError();
 }
@@ -514,24 +633,24 @@ bool block_mode_supported(int k, bool f64)
     if (k < 1 || k > 32) return false;
     const int kt = block_kt_for(k);
     int kc, P;
-    block_geometry(32, kt, f64, &kc, &P);
-    return block_smem_bytes(32, kt, kc, f64) <= kBlockSmemBudget;
+    block_geometry(32, kt, f64, kMaxBlockWarps, &kc, &P);
+    return block_smem_bytes(32, kt, kc, f64, kMaxBlockWarps) <= kBlockSmemBudget;
 }
 
 template <class T>
 cudaError_t solve_block(const Sys<T> &A, const Rhs<T> &R, int rpw, int kt, bool trans,
-                        const SyncArgs &sy, cudaStream_t s)
+                        const SyncArgs &sy, int nwarps, cudaStream_t s)
 {
     (void)kt;
     cudaError_t e = launch_prologue<T>(sy.ctl, s);
     if (e != cudaSuccess || A.n <= 0) return e;
     switch (block_kt_for(R.k)) {
-    case 1: return blk_launch<T, 1>(A, R, rpw, trans, sy, s);
-    case 2: return blk_launch<T, 2>(A, R, rpw, trans, sy, s);
-    case 4: return blk_launch<T, 4>(A, R, rpw, trans, sy, s);
-    case 8: return blk_launch<T, 8>(A, R, rpw, trans, sy, s);
-    case 16: return blk_launch<T, 16>(A, R, rpw, trans, sy, s);
-    default: return blk_launch<T, 32>(A, R, rpw, trans, sy, s);
+    case 1: return blk_launch<T, 1>(A, R, rpw, trans, sy, nwarps, s);
+    case 2: return blk_launch<T, 2>(A, R, rpw, trans, sy, nwarps, s);
+    case 4: return blk_launch<T, 4>(A, R, rpw, trans, sy, nwarps, s);
+    case 8: return blk_launch<T, 8>(A, R, rpw, trans, sy, nwarps, s);
+    case 16: return blk_launch<T, 16>(A, R, rpw, trans, sy, nwarps, s);
+    default: return blk_launch<T, 32>(A, R, rpw, trans, sy, nwarps, s);
     }
 }
 
@@ -566,7 +685,7 @@ int persistent_grid_syncfree(int kt, bool f64, const DeviceInfo &di)
     template cudaError_t solve_syncfree<T>(const Sys<T> &, const Rhs<T> &, int, int, bool,              \
                                            const SyncArgs &, int, cudaStream_t);                        \
     template cudaError_t solve_block<T>(const Sys<T> &, const Rhs<T> &, int, int, bool,                 \
-                                        const SyncArgs &, cudaStream_t);                                \
+                                        const SyncArgs &, int, cudaStream_t);                           \
     template cudaError_t grad_vals<T>(const Sys<T> &, const T *, const T *, int64_t, int32_t, T *,      \
                                       cudaStream_t);                                                    \
     template cudaError_t tt_apply<T>(const Sys<T> &, const T *, T *, int64_t, int32_t, cudaStream_t);

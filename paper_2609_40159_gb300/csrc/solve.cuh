@@ -76,7 +76,7 @@ cudaError_t solve_syncfree(const Sys<T> &A, const Rhs<T> &R, int rpw, int kt, bo
 
 template <class T>
 cudaError_t solve_block(const Sys<T> &A, const Rhs<T> &R, int rpw, int kt, bool trans,
-                        const SyncArgs &sy, cudaStream_t s);
+                        const SyncArgs &sy, int nwarps, cudaStream_t s);
 
 template <class T>
 cudaError_t grad_vals(const Sys<T> &A, const T *gb, const T *x, int64_t ld, int32_t k, T *gv,
@@ -96,9 +96,14 @@ int persistent_grid_syncfree(int kt, bool f64, const DeviceInfo &di);
 // Block mode: whether (k, dtype) fits the shared-memory ring.
 bool block_mode_supported(int k, bool f64);
 int block_kt_for(int k);
-// Ring geometry of the block mode: kc row groups in the ring, throttle P.
-void block_geometry(int rpw, int kt, bool f64, int *kc, int *P);
-size_t block_smem_bytes(int rpw, int kt, int kc, bool f64);
+// Ring geometry of the block mode for `nwarps` active warps: kc row groups in
+// the ring, throttle distance P.
+void block_geometry(int rpw, int kt, bool f64, int nwarps, int *kc, int *P);
+// Active warps of the block mode for a system with the given level width.
+int block_warps_for(double rows_per_level, int rpw);
+size_t block_smem_bytes(int rpw, int kt, int kc, bool f64, int nw);
+// Most warps of a block-mode thread block that work on one system.
+constexpr int kMaxBlockWarps = 8;
 constexpr size_t kBlockSmemBudget = 200 * 1024;
 
 // ---------------------------------------------------------------- batched
@@ -110,6 +115,7 @@ struct BatchMat {
     int32_t kt;       // rhs register tile (>= k)
     int32_t kc;       // ring row groups (block mode)
     int32_t P;        // throttle distance in row groups
+    int32_t nw;       // active warps of the thread block
     int64_t nnz;
     const int32_t *rp, *ci;
     const void *v;
@@ -127,7 +133,7 @@ struct BatchMat {
 template <class T>
 cudaError_t batch_solve(const BatchMat *mats, int32_t nmat, const int32_t *order, const T *b,
                         T *x, bool trans, PlanCtl *ctl, const Waiter &w, int grid,
-                        size_t smem, cudaStream_t s);
+                        size_t smem, long long *trace, cudaStream_t s);
 // Value gradients of all matrices (row_off: nmat+1 prefix of n, device).
 template <class T>
 cudaError_t batch_grad_vals(const BatchMat *mats, int32_t nmat, const int64_t *row_off,
