@@ -254,7 +254,7 @@ def main():
 
     tune = None
     if not args.no_tune and not args.ncu:
-        tune = autotune.tune_batch(bplan, b, candidates=(8, 16, 32), reps=3)
+        tune = autotune.tune_batch(bplan, b, candidates=(8, 16, 32), tiles=(2, 4, 8), reps=3)
 
     # algorithmic bytes
     wv = 4
@@ -271,7 +271,9 @@ def main():
     with torch.cuda.stream(s):
         gplan = P.BatchPlan(mats, Ts, nrhs, transpose=True)
         if tune is not None:
-            gplan.set_rows_per_warp([tune["choice"][l] for l in autotune.batch_classes(gplan)])
+            labels = autotune.batch_classes(gplan)
+            gplan.set_geometry([tune["choice"][l]["rows_per_warp"] for l in labels],
+                               [tune["choice"][l]["rhs_tile"] for l in labels])
         for _ in range(2):
             gplan.solve(b, out=x)
             gplan.solve_transpose(w, out=gbp)

@@ -96,7 +96,10 @@ typedef enum {
 typedef struct {
     int32_t mode;            /* sptrsv_mode; AUTO picks from the level profile */
     int32_t rows_per_warp;   /* 1,2,4,8,16,32 (lanes per row = 32/rows_per_warp); 0 = auto */
-    int32_t rhs_tile;        /* right-hand sides per pass: 1,2,4,8,16; 0 = auto */
+    int32_t rhs_tile;        /* right-hand sides per pass: 1,2,4,8,16; 0 = auto.
+                                Block mode and batched plans: columns per
+                                thread block (1,2,4,8); wider right-hand
+                                sides run as independent column tiles      */
     int32_t build_transpose; /* non-zero: prepare sptrsv_solve_transpose / grad  */
     int64_t wait_limit_us;   /* longest a device wait may take before the solve
                                 gives up with SPTRSV_ETIMEOUT (microseconds);
@@ -205,10 +208,17 @@ sptrsv_status sptrsv_batch_plan_create(sptrsv_handle handle, int32_t nmat, const
                                        const sptrsv_csr *Ts, const int32_t *nrhs,
                                        const sptrsv_plan_opts *opts, sptrsv_plan *plan);
 sptrsv_status sptrsv_batch_offsets(sptrsv_plan plan, int64_t *rhs_offset, int64_t *vals_offset);
-/* Re-tunes a batched plan: rows_per_warp (host, nmat entries; 0 = keep) is
- * the row-group width of every system (used by the autotuner; no analysis
- * is repeated).  Synchronises.                                             */
-sptrsv_status sptrsv_batch_plan_set(sptrsv_plan plan, const int32_t *rows_per_warp);
+/* Re-tunes a batched plan (used by the autotuner; no analysis is repeated).
+ *   rows_per_warp  host, nmat entries (1,2,4,8,16,32; 0 = keep) or NULL:
+ *                  row-group width of every system;
+ *   rhs_tile       host, nmat entries (1,2,4,8; 0 = keep) or NULL: columns
+ *                  per work item; system m runs as ceil(nrhs_m / rhs_tile_m)
+ *                  independent work items.
+ * Returns SPTRSV_EINVAL for a value outside those sets, SPTRSV_ENOTSUP when
+ * the geometry does not fit in shared memory (the plan keeps its previous
+ * geometry).  Synchronises.                                               */
+sptrsv_status sptrsv_batch_plan_set(sptrsv_plan plan, const int32_t *rows_per_warp,
+                                    const int32_t *rhs_tile);
 /* All systems in one persistent launch (plus a tiny reset launch): no host
  * work per matrix, so the call can be captured in a CUDA graph.            */
 sptrsv_status sptrsv_batch_solve(sptrsv_plan plan, const void *b, void *x);

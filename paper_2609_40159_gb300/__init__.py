@@ -7,10 +7,11 @@ touch the GPU; the first call that needs the library loads
 ``libsptrsv_gb300.so`` and raises if it has not been built.
 """
 from . import _lib
+from ._lib import SpTRSVError
 from .api import Analysis, BatchPlan, Handle, Matrix, Plan, analyze, handle, rewrite, validate
 from .autograd import BatchSpTRSVFunction, SpTRSVFunction, batch_solve, solve
 
 __all__ = [
-    "_lib", "Analysis", "BatchPlan", "Handle", "Matrix", "Plan", "analyze", "handle", "rewrite",
+    "_lib", "SpTRSVError", "Analysis", "BatchPlan", "Handle", "Matrix", "Plan", "analyze", "handle", "rewrite",
     "validate", "SpTRSVFunction", "BatchSpTRSVFunction", "solve", "batch_solve",
 ]

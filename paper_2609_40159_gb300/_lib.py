@@ -100,7 +100,7 @@ _SIGS = {
     "sptrsv_batch_plan_create": [sptrsv_handle, _I32, C.POINTER(sptrsv_csr), C.POINTER(sptrsv_csr),
                                  _PI32, C.POINTER(sptrsv_plan_opts), C.POINTER(sptrsv_plan)],
     "sptrsv_batch_offsets": [sptrsv_plan, _PI64, _PI64],
-    "sptrsv_batch_plan_set": [sptrsv_plan, _PI32],
+    "sptrsv_batch_plan_set": [sptrsv_plan, _PI32, _PI32],
     "sptrsv_batch_solve": [sptrsv_plan, _P, _P],
     "sptrsv_batch_solve_transpose": [sptrsv_plan, _P, _P],
     "sptrsv_batch_grad_vals": [sptrsv_plan, _P, _P, _P],

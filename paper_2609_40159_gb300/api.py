@@ -236,11 +236,18 @@ class Plan:
             pass
 
 
+def _per_system(v, m):
+    if v is None:
+        return 0
+    return int(v[m] if hasattr(v, "__len__") else v)
+
+
 class BatchPlan:
     """One plan over many independent systems; right-hand sides, solutions
     and gradients are packed (see sptrsv_batch_plan_create)."""
 
-    def __init__(self, mats, Ts=None, nrhs=None, rows_per_warp=None, transpose=False, wait_limit_us=0):
+    def __init__(self, mats, Ts=None, nrhs=None, rows_per_warp=None, transpose=False, wait_limit_us=0,
+                 rhs_tile=None):
         nmat = len(mats)
         self.mats, self.Ts = list(mats), list(Ts) if Ts is not None else [None] * nmat
         self.nrhs = [int(k) for k in (nrhs if nrhs is not None else [1] * nmat)]
@@ -251,8 +258,9 @@ class BatchPlan:
             descs[m] = A.desc()
             T = self.Ts[m]
             tdescs[m] = T.desc() if T is not None else L.sptrsv_csr(0, 0, None, None, None, 0)
-            rpw = 0 if rows_per_warp is None else int(rows_per_warp[m] if hasattr(rows_per_warp, "__len__") else rows_per_warp)
-            opts[m] = L.sptrsv_plan_opts(L.SPTRSV_MODE_BLOCK, rpw, 0, 1 if transpose else 0, wait_limit_us)
+            rpw = _per_system(rows_per_warp, m)
+            tile = _per_system(rhs_tile, m)
+            opts[m] = L.sptrsv_plan_opts(L.SPTRSV_MODE_BLOCK, rpw, tile, 1 if transpose else 0, wait_limit_us)
         ks = (C.c_int32 * max(nmat, 1))(*self.nrhs)
         self._h = handle()
         p = L.sptrsv_plan()
@@ -266,12 +274,22 @@ class BatchPlan:
         self.vals_offset = np.array(list(vo), dtype=np.int64)
         self.dtype = mats[0].dtype if nmat else torch.float32
 
+    def set_geometry(self, rows_per_warp=None, rhs_tile=None):
+        """Row-group width and right-hand-side columns per work item, per
+        system (list) or for all systems (int); None or 0 keeps the value."""
+        nmat = len(self.mats)
+
+        def arr(v):
+            if v is None:
+                return None
+            return (C.c_int32 * max(nmat, 1))(*[_per_system(v, m) for m in range(nmat)])
+
+        L.check(L.lib().sptrsv_batch_plan_set(self.p, arr(rows_per_warp), arr(rhs_tile)),
+                "sptrsv_batch_plan_set")
+
     def set_rows_per_warp(self, rpw):
         """Row-group width per system (list) or for all systems (int)."""
-        nmat = len(self.mats)
-        vals = [int(rpw)] * nmat if not hasattr(rpw, "__len__") else [int(r) for r in rpw]
-        arr = (C.c_int32 * max(nmat, 1))(*vals)
-        L.check(L.lib().sptrsv_batch_plan_set(self.p, arr), "sptrsv_batch_plan_set")
+        self.set_geometry(rows_per_warp=rpw)
 
     @property
     def total_rhs(self):

@@ -16,6 +16,7 @@ import os
 import numpy as np
 import torch
 
+from . import _lib as L
 from .api import BatchPlan, Plan
 
 CANDIDATE_MODES = ("level", "syncfree", "block")
@@ -114,32 +115,39 @@ def batch_classes(bplan: BatchPlan):
     return labels
 
 
-def tune_batch(bplan: BatchPlan, b: torch.Tensor, candidates=(8, 16, 32), reps=3, rounds=1):
-    """Per size class rows-per-warp for the batched solve (coordinate descent:
-    each class tries every candidate with the others fixed)."""
+def tune_batch(bplan: BatchPlan, b: torch.Tensor, candidates=(8, 16, 32), tiles=(2, 4, 8), reps=3,
+               rounds=1):
+    """Per size class rows-per-warp and right-hand-side tile of the batched
+    solve (coordinate descent: each class tries every candidate of one knob
+    with everything else fixed)."""
     labels = batch_classes(bplan)
     classes = sorted(set(labels))
-    choice = {c: 32 for c in classes}
+    choice = {c: [32, 8] for c in classes}
     x = torch.empty_like(b)
 
     def apply():
-        bplan.set_rows_per_warp([choice[l] for l in labels])
+        bplan.set_geometry([choice[l][0] for l in labels], [choice[l][1] for l in labels])
 
     apply()
     best_ms = time_call(lambda: bplan.solve(b, out=x), reps=reps)
     log = [dict(step="start", ms=best_ms)]
     for _ in range(rounds):
         for c in classes:
-            keep = choice[c]
-            for cand in candidates:
-                if cand == keep:
-                    continue
-                choice[c] = cand
+            for knob, cands in ((0, candidates), (1, tiles)):
+                keep = choice[c][knob]
+                for cand in cands:
+                    if cand == keep:
+                        continue
+                    choice[c][knob] = cand
+                    try:
+                        apply()
+                    except L.SpTRSVError:
+                        continue
+                    ms = time_call(lambda: bplan.solve(b, out=x), reps=reps)
+                    log.append(dict(cls=c, knob=("rows_per_warp", "rhs_tile")[knob], value=cand, ms=ms))
+                    if ms < best_ms * 0.995:
+                        best_ms, keep = ms, cand
+                choice[c][knob] = keep
                 apply()
-                ms = time_call(lambda: bplan.solve(b, out=x), reps=reps)
-                log.append(dict(cls=c, rpw=cand, ms=ms))
-                if ms < best_ms * 0.995:
-                    best_ms, keep = ms, cand
-            choice[c] = keep
-            apply()
-    return dict(choice=choice, ms=best_ms, log=log)
+    return dict(choice={c: dict(rows_per_warp=v[0], rhs_tile=v[1]) for c, v in choice.items()}, ms=best_ms,
+                log=log)

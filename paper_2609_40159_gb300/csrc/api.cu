@@ -107,9 +107,12 @@ struct sptrsv_plan_st {
     std::vector<int64_t> rhs_off, vals_off, row_off;
     BatchMat *d_mats = nullptr;
     std::vector<BatchMat> h_mats;
+    std::vector<int32_t> b_rpw, b_tile;  // per system: rows per warp, rhs columns per work item
+    BatchItem *d_items = nullptr;        // work items: (system, rhs column tile) and its geometry
+    int32_t nitems = 0, max_items = 0;
     int32_t *d_order = nullptr;
     int64_t *d_row_off = nullptr;
-    long long *d_trace = nullptr;  // per system: start ns, end ns, SM of the last batch solve
+    long long *d_trace = nullptr;  // per work item: start ns, end ns, SM of the last batch solve
     size_t batch_smem = 0;
     int batch_grid_sz = 0;
 
@@ -506,8 +509,8 @@ extern "C" sptrsv_status sptrsv_plan_info(sptrsv_plan p, int32_t *nlevels, int32
         }
     }
     if (mode) *mode = p->batched ? SPTRSV_MODE_BLOCK : p->mode;
-    if (rows_per_warp) *rows_per_warp = p->rpw;
-    if (rhs_tile) *rhs_tile = p->kt;
+    if (rows_per_warp) *rows_per_warp = p->batched ? (p->b_rpw.empty() ? 32 : p->b_rpw[0]) : p->rpw;
+    if (rhs_tile) *rhs_tile = p->batched ? (p->b_tile.empty() ? 8 : p->b_tile[0]) : p->kt;
     return SPTRSV_OK;
 }
 
@@ -574,6 +577,66 @@ extern "C" sptrsv_status sptrsv_debug_withhold_row(sptrsv_plan p, int32_t row)
 }
 
 // ----------------------------------------------------------------- batched
+namespace {
+bool valid_tile(int t) { return t == 1 || t == 2 || t == 4 || t == 8; }
+
+int pow2_at_least(int v)
+{
+    int k = 1;
+    while (k < v) k <<= 1;
+    return k;
+}
+
+// Work items of a batch: every system is split into tiles of at most b_tile
+// right-hand-side columns, each an independent in-order chain solved by one
+// thread block.  Builds the items with their geometry, orders them longest
+// estimated chain first (LPT), and sizes shared memory and the grid.
+sptrsv_status rebuild_items(sptrsv_plan p)
+{
+    const int32_t nmat = (int32_t)p->mats.size();
+    const bool f64 = p->dtype == SPTRSV_F64;
+    std::vector<BatchItem> items;
+    std::vector<double> est;
+    size_t smem = 16;
+    for (int m = 0; m < nmat; ++m) {
+        const PlanMat &M = p->mats[m];
+        const int k = p->h_mats[m].k;
+        const int tile = p->b_tile[m];
+        for (int r0 = 0; r0 < k; r0 += tile) {
+            BatchItem I{};
+            I.mat = m;
+            I.r0 = r0;
+            I.kt = std::min(tile, k - r0);
+            I.KT = pow2_at_least(I.kt);
+            I.rpw = p->b_rpw[m];
+            I.nw = block_warps_for(M.nlevels > 0 ? (double)M.L.n / M.nlevels : 1.0, I.rpw);
+            block_geometry(I.rpw, I.KT, f64, I.nw, &I.kc, &I.P);
+            smem = std::max(smem, block_smem_bytes(I.rpw, I.KT, I.kc, f64, I.nw));
+            items.push_back(I);
+            // chain of n / 32 row groups whose cost grows with the tile width,
+            // plus the streamed matrix
+            est.push_back((double)M.L.n * (1.0 + 0.1 * I.KT) + 0.01 * (double)M.L.nnz);
+        }
+    }
+    if (smem > kBlockSmemBudget) return SPTRSV_ENOTSUP;
+    const int32_t ni = (int32_t)items.size();
+    if (ni > p->max_items) return SPTRSV_EINVAL;
+    std::vector<int32_t> order((size_t)ni);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return est[x] > est[y]; });
+    cudaError_t e = cudaStreamSynchronize(p->h->stream);
+    if (e == cudaSuccess && ni > 0)
+        e = cudaMemcpy(p->d_items, items.data(), sizeof(BatchItem) * ni, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && ni > 0)
+        e = cudaMemcpy(p->d_order, order.data(), sizeof(int32_t) * ni, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return from_cuda(e);
+    p->nitems = ni;
+    p->batch_smem = smem;
+    p->batch_grid_sz = std::min(batch_grid(smem, p->h->di), std::max(ni, 1));
+    return SPTRSV_OK;
+}
+}  // namespace
+
 extern "C" sptrsv_status sptrsv_batch_plan_create(sptrsv_handle h, int32_t nmat, const sptrsv_csr *Ls,
                                                   const sptrsv_csr *Ts, const int32_t *nrhs,
                                                   const sptrsv_plan_opts *opts, sptrsv_plan *plan)
@@ -596,26 +659,23 @@ extern "C" sptrsv_status sptrsv_batch_plan_create(sptrsv_handle h, int32_t nmat,
     p->rhs_off.assign((size_t)nmat + 1, 0);
     p->vals_off.assign((size_t)nmat + 1, 0);
     p->row_off.assign((size_t)nmat + 1, 0);
-    std::vector<BatchMat> hm((size_t)nmat);
-    std::vector<double> est((size_t)nmat);
-    size_t smem = 16;
-    const bool f64 = p->dtype == SPTRSV_F64;
+    p->h_mats.resize((size_t)nmat);
+    p->b_rpw.assign((size_t)nmat, 32);
+    p->b_tile.assign((size_t)nmat, 8);
+    int64_t ktot = 0;
     for (int m = 0; m < nmat; ++m) {
         sptrsv_status st = check_csr(&Ls[m]);
-        if (st == SPTRSV_OK && (Ls[m].dtype != p->dtype || nrhs[m] < 1 || !block_mode_supported(nrhs[m], f64)))
-            st = nrhs[m] < 1 || Ls[m].dtype != p->dtype ? SPTRSV_EINVAL : SPTRSV_ENOTSUP;
+        if (st == SPTRSV_OK && (Ls[m].dtype != p->dtype || nrhs[m] < 1)) st = SPTRSV_EINVAL;
+        if (st == SPTRSV_OK && opts && opts[m].rows_per_warp != 0 && !valid_rpw(opts[m].rows_per_warp))
+            st = SPTRSV_EINVAL;
+        if (st == SPTRSV_OK && opts && opts[m].rhs_tile != 0 && !valid_tile(opts[m].rhs_tile))
+            st = SPTRSV_EINVAL;
         if (st == SPTRSV_OK) st = prepare_mat(p, p->mats[m], Ls[m], Ts ? &Ts[m] : nullptr, want_csc);
         if (st != SPTRSV_OK) { sptrsv_plan_destroy(p); return st; }
         const PlanMat &M = p->mats[m];
-        BatchMat &B = hm[m];
+        BatchMat &B = p->h_mats[m];
         B.n = M.L.n;
         B.k = nrhs[m];
-        const int orpw = opts ? opts[m].rows_per_warp : 0;
-        B.rpw = valid_rpw(orpw) ? orpw : default_rpw(M.L.n, M.L.nnz);
-        B.kt = block_kt_for(B.k);
-        B.nw = block_warps_for(M.nlevels > 0 ? (double)M.L.n / M.nlevels : 1.0, B.rpw);
-        block_geometry(B.rpw, B.kt, f64, B.nw, &B.kc, &B.P);
-        smem = std::max(smem, block_smem_bytes(B.rpw, B.kt, B.kc, f64, B.nw));
         B.nnz = M.L.nnz;
         B.rp = M.L.row_ptr; B.ci = M.L.col_idx; B.v = M.L.vals;
         B.cp = M.d_cp; B.crow = M.d_crow; B.tmap = M.d_tmap;
@@ -629,52 +689,49 @@ extern "C" sptrsv_status sptrsv_batch_plan_create(sptrsv_handle h, int32_t nmat,
         p->rhs_off[m + 1] = p->rhs_off[m] + (int64_t)M.L.n * B.k;
         p->vals_off[m + 1] = p->vals_off[m] + M.L.nnz;
         p->row_off[m + 1] = p->row_off[m] + M.L.n;
-        // critical path estimate: levels x hop latency vs streamed bytes
-        est[m] = (double)M.nlevels * 150.0 + (double)(M.L.nnz + (int64_t)M.L.n * B.k) * 0.05;
+        p->b_rpw[m] = opts && opts[m].rows_per_warp ? opts[m].rows_per_warp : default_rpw(M.L.n, M.L.nnz);
+        if (opts && opts[m].rhs_tile) p->b_tile[m] = opts[m].rhs_tile;
+        ktot += B.k;
     }
     p->have_csc = want_csc;
-    std::vector<int32_t> order((size_t)nmat);
-    std::iota(order.begin(), order.end(), 0);
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return est[a] > est[b]; });
+    p->max_items = (int32_t)std::max<int64_t>(ktot, 1);  // tiles of one column at most
     e = p->alloc(&p->d_mats, sizeof(BatchMat) * (size_t)(nmat > 0 ? nmat : 1));
-    if (e == cudaSuccess) e = p->alloc(&p->d_order, sizeof(int32_t) * (size_t)(nmat > 0 ? nmat : 1));
+    if (e == cudaSuccess) e = p->alloc(&p->d_items, sizeof(BatchItem) * (size_t)p->max_items);
+    if (e == cudaSuccess) e = p->alloc(&p->d_order, sizeof(int32_t) * (size_t)p->max_items);
     if (e == cudaSuccess) e = p->alloc(&p->d_row_off, sizeof(int64_t) * ((size_t)nmat + 1));
-    if (e == cudaSuccess) e = p->alloc(&p->d_trace, sizeof(long long) * 3 * (size_t)(nmat > 0 ? nmat : 1));
-    if (e == cudaSuccess && nmat > 0) e = cudaMemcpy(p->d_mats, hm.data(), sizeof(BatchMat) * nmat, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess && nmat > 0) e = cudaMemcpy(p->d_order, order.data(), sizeof(int32_t) * nmat, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(p->d_row_off, p->row_off.data(), sizeof(int64_t) * (nmat + 1), cudaMemcpyHostToDevice);
-    if (e != cudaSuccess || smem > kBlockSmemBudget) { sptrsv_plan_destroy(p); return e != cudaSuccess ? from_cuda(e) : SPTRSV_ENOTSUP; }
-    p->batch_smem = smem;
-    p->batch_grid_sz = std::min(batch_grid(smem, h->di), std::max(nmat, 1));
-    p->h_mats = hm;
+    if (e == cudaSuccess) e = p->alloc(&p->d_trace, sizeof(long long) * 3 * (size_t)p->max_items);
+    if (e == cudaSuccess && nmat > 0)
+        e = cudaMemcpy(p->d_mats, p->h_mats.data(), sizeof(BatchMat) * nmat, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(p->d_row_off, p->row_off.data(), sizeof(int64_t) * (nmat + 1), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) { sptrsv_plan_destroy(p); return from_cuda(e); }
+    sptrsv_status st = rebuild_items(p);
+    if (st != SPTRSV_OK) { sptrsv_plan_destroy(p); return st; }
     *plan = p;
     return SPTRSV_OK;
 }
 
-extern "C" sptrsv_status sptrsv_batch_plan_set(sptrsv_plan p, const int32_t *rows_per_warp)
+extern "C" sptrsv_status sptrsv_batch_plan_set(sptrsv_plan p, const int32_t *rows_per_warp,
+                                               const int32_t *rhs_tile)
 {
-    if (!p || !p->batched || !rows_per_warp) return SPTRSV_EINVAL;
+    if (!p || !p->batched) return SPTRSV_EINVAL;
     const int32_t nmat = (int32_t)p->h_mats.size();
-    const bool f64 = p->dtype == SPTRSV_F64;
-    for (int m = 0; m < nmat; ++m)
-        if (rows_per_warp[m] != 0 && !valid_rpw(rows_per_warp[m])) return SPTRSV_EINVAL;
-    size_t smem = 16;
     for (int m = 0; m < nmat; ++m) {
-        BatchMat &B = p->h_mats[m];
-        if (rows_per_warp[m]) B.rpw = rows_per_warp[m];
-        const PlanMat &M = p->mats[m];
-        B.nw = block_warps_for(M.nlevels > 0 ? (double)M.L.n / M.nlevels : 1.0, B.rpw);
-        block_geometry(B.rpw, B.kt, f64, B.nw, &B.kc, &B.P);
-        smem = std::max(smem, block_smem_bytes(B.rpw, B.kt, B.kc, f64, B.nw));
+        if (rows_per_warp && rows_per_warp[m] != 0 && !valid_rpw(rows_per_warp[m])) return SPTRSV_EINVAL;
+        if (rhs_tile && rhs_tile[m] != 0 && !valid_tile(rhs_tile[m])) return SPTRSV_EINVAL;
     }
-    if (smem > kBlockSmemBudget) return SPTRSV_ENOTSUP;
-    cudaError_t e = cudaStreamSynchronize(p->h->stream);
-    if (e == cudaSuccess && nmat > 0)
-        e = cudaMemcpy(p->d_mats, p->h_mats.data(), sizeof(BatchMat) * nmat, cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) return from_cuda(e);
-    p->batch_smem = smem;
-    p->batch_grid_sz = std::min(batch_grid(smem, p->h->di), std::max(nmat, 1));
-    return SPTRSV_OK;
+    const std::vector<int32_t> old_rpw = p->b_rpw, old_tile = p->b_tile;
+    for (int m = 0; m < nmat; ++m) {
+        if (rows_per_warp && rows_per_warp[m]) p->b_rpw[m] = rows_per_warp[m];
+        if (rhs_tile && rhs_tile[m]) p->b_tile[m] = rhs_tile[m];
+    }
+    sptrsv_status st = rebuild_items(p);
+    if (st == SPTRSV_ENOTSUP) {  // geometry does not fit: keep the previous one
+        p->b_rpw = old_rpw;
+        p->b_tile = old_tile;
+        if (rebuild_items(p) != SPTRSV_OK) return SPTRSV_ECUDA;
+    }
+    return st;
 }
 
 extern "C" sptrsv_status sptrsv_batch_offsets(sptrsv_plan p, int64_t *rhs_offset, int64_t *vals_offset)
@@ -689,18 +746,17 @@ namespace {
 sptrsv_status batch_solve_impl(sptrsv_plan p, const void *b, void *x, bool trans)
 {
     if (!p || !p->batched) return SPTRSV_EINVAL;
-    const int32_t nmat = (int32_t)p->mats.size();
-    if (nmat == 0) return SPTRSV_OK;
+    if (p->nitems == 0) return SPTRSV_OK;
     if (!b || !x) return SPTRSV_EINVAL;
     if (trans && !p->have_csc) return SPTRSV_ENOTSUP;
     Waiter w{p->h->d_status, &p->d_ctl->abort_flag, p->spin};
     cudaError_t e;
     if (p->dtype == SPTRSV_F64)
-        e = batch_solve<double>(p->d_mats, nmat, p->d_order, (const double *)b, (double *)x, trans, p->d_ctl, w,
-                                p->batch_grid_sz, p->batch_smem, p->d_trace, p->h->stream);
+        e = batch_solve<double>(p->d_mats, p->d_items, p->nitems, p->d_order, (const double *)b, (double *)x,
+                                trans, p->d_ctl, w, p->batch_grid_sz, p->batch_smem, p->d_trace, p->h->stream);
     else
-        e = batch_solve<float>(p->d_mats, nmat, p->d_order, (const float *)b, (float *)x, trans, p->d_ctl, w,
-                               p->batch_grid_sz, p->batch_smem, p->d_trace, p->h->stream);
+        e = batch_solve<float>(p->d_mats, p->d_items, p->nitems, p->d_order, (const float *)b, (float *)x,
+                               trans, p->d_ctl, w, p->batch_grid_sz, p->batch_smem, p->d_trace, p->h->stream);
     return debug_sync(from_cuda(e), p->h->stream, "batch_solve");
 }
 }  // namespace
@@ -720,10 +776,30 @@ extern "C" sptrsv_status sptrsv_batch_trace(sptrsv_plan p, int64_t *trace)
     if (!p || !p->batched || !trace) return SPTRSV_EINVAL;
     const size_t nmat = p->mats.size();
     if (nmat == 0) return SPTRSV_OK;
+    std::vector<long long> t(3 * (size_t)p->nitems);
+    std::vector<BatchItem> items((size_t)p->nitems);
     cudaError_t e = cudaStreamSynchronize(p->h->stream);
-    if (e == cudaSuccess)
-        e = cudaMemcpy(trace, p->d_trace, sizeof(long long) * 3 * nmat, cudaMemcpyDeviceToHost);
-    return from_cuda(e);
+    if (e == cudaSuccess && p->nitems > 0)
+        e = cudaMemcpy(t.data(), p->d_trace, sizeof(long long) * t.size(), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && p->nitems > 0)
+        e = cudaMemcpy(items.data(), p->d_items, sizeof(BatchItem) * items.size(), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return from_cuda(e);
+    // per system: earliest start and latest end over its work items, and the
+    // SM that started first
+    for (size_t m = 0; m < nmat; ++m) {
+        trace[3 * m] = INT64_MAX;
+        trace[3 * m + 1] = 0;
+        trace[3 * m + 2] = -1;
+    }
+    for (int32_t it = 0; it < p->nitems; ++it) {
+        const int m = items[(size_t)it].mat;
+        if (t[3 * (size_t)it] < trace[3 * m]) {
+            trace[3 * m] = t[3 * (size_t)it];
+            trace[3 * m + 2] = t[3 * (size_t)it + 2];
+        }
+        trace[3 * m + 1] = std::max<int64_t>(trace[3 * m + 1], t[3 * (size_t)it + 1]);
+    }
+    return SPTRSV_OK;
 }
 
 extern "C" sptrsv_status sptrsv_batch_grad_vals(sptrsv_plan p, const void *gb, const void *x, void *gvals)

@@ -9,7 +9,7 @@ namespace spt {
 
 namespace {
 
-constexpr int kBatchThreads = 512;
+constexpr int kBatchThreads = 32 * kMaxBlockWarps;
 
 template <class T>
 __device__ __forceinline__ Sys<T> sys_of(const BatchMat &M)
@@ -23,19 +23,19 @@ __device__ __forceinline__ Sys<T> sys_of(const BatchMat &M)
 }
 
 template <class T, int KT, bool TR>
-__device__ __forceinline__ bool run_one(const BatchMat &M, unsigned char *raw, const T *b, T *x,
-                                        const Waiter &w)
+__device__ __forceinline__ bool run_one(const BatchMat &M, const BatchItem &I, unsigned char *raw,
+                                        const T *b, T *x, const Waiter &w)
 {
-    const int ring = M.kc * M.rpw;
-    BlockSmem<T, KT> sm = carve_block_smem<T, KT>(raw, ring, M.kc, M.nw);
-    reset_block_smem<T, KT>(sm, ring, M.kc);
+    const int ring = I.kc * I.rpw;
+    BlockSmem<T, KT> sm = carve_block_smem<T, KT>(raw, ring, I.kc, I.nw);
+    reset_block_smem<T, KT>(sm, ring, I.kc);
     __syncthreads();
     Rhs<T> R;
-    R.b = b + M.rhs_off;
-    R.x = x + M.rhs_off;
+    R.b = b + M.rhs_off + I.r0;
+    R.x = x + M.rhs_off + I.r0;
     R.ld = M.k;
-    R.k = M.k;
-    return block_solve_any<T, KT, TR>(sys_of<T>(M), R, M.rpw, M.kc, M.P, M.nw, sm, w, -1);
+    R.k = I.kt;
+    return block_solve_any<T, KT, TR>(sys_of<T>(M), R, I.rpw, I.kc, I.P, I.nw, sm, w, -1);
 }
 
 __device__ __forceinline__ unsigned sm_id()
@@ -47,8 +47,9 @@ __device__ __forceinline__ unsigned sm_id()
 
 template <class T, bool TR>
 __global__ void __launch_bounds__(kBatchThreads)
-k_batch(const BatchMat *__restrict__ mats, int32_t nmat, const int32_t *__restrict__ order,
-        const T *b, T *x, PlanCtl *ctl, Waiter w, long long *trace)
+k_batch(const BatchMat *__restrict__ mats, const BatchItem *__restrict__ items, int32_t nitems,
+        const int32_t *__restrict__ order, const T *b, T *x, PlanCtl *ctl, Waiter w,
+        long long *trace)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ int s_next, s_stop;
@@ -61,23 +62,22 @@ k_batch(const BatchMat *__restrict__ mats, int32_t nmat, const int32_t *__restri
         const int t = s_next;
         const int stop = s_stop;
         __syncthreads();
-        if (t >= nmat || stop) return;
-        const int m = order[t];
-        const BatchMat M = mats[m];
+        if (t >= nitems || stop) return;
+        const int it = order[t];
+        const BatchItem I = items[it];
+        const BatchMat M = mats[I.mat];
         if (trace && threadIdx.x == 0) {
-            trace[3 * m] = (long long)now_ns();
-            trace[3 * m + 2] = (long long)sm_id();
+            trace[3 * it] = (long long)now_ns();
+            trace[3 * it + 2] = (long long)sm_id();
         }
-        switch (M.kt) {
-        case 1: run_one<T, 1, TR>(M, smraw, b, x, w); break;
-        case 2: run_one<T, 2, TR>(M, smraw, b, x, w); break;
-        case 4: run_one<T, 4, TR>(M, smraw, b, x, w); break;
-        case 8: run_one<T, 8, TR>(M, smraw, b, x, w); break;
-        case 16: run_one<T, 16, TR>(M, smraw, b, x, w); break;
-        default: run_one<T, 32, TR>(M, smraw, b, x, w); break;
+        switch (I.KT) {
+        case 1: run_one<T, 1, TR>(M, I, smraw, b, x, w); break;
+        case 2: run_one<T, 2, TR>(M, I, smraw, b, x, w); break;
+        case 4: run_one<T, 4, TR>(M, I, smraw, b, x, w); break;
+        default: run_one<T, 8, TR>(M, I, smraw, b, x, w); break;
         }
         __syncthreads();
-        if (trace && threadIdx.x == 0) trace[3 * m + 1] = (long long)now_ns();
+        if (trace && threadIdx.x == 0) trace[3 * it + 1] = (long long)now_ns();
     }
 }
 
@@ -164,17 +164,17 @@ int batch_grid(size_t smem, const DeviceInfo &di)
 }
 
 template <class T>
-cudaError_t batch_solve(const BatchMat *mats, int32_t nmat, const int32_t *order, const T *b,
-                        T *x, bool trans, PlanCtl *ctl, const Waiter &w, int grid,
-                        size_t smem, long long *trace, cudaStream_t s)
+cudaError_t batch_solve(const BatchMat *mats, const BatchItem *items, int32_t nitems,
+                        const int32_t *order, const T *b, T *x, bool trans, PlanCtl *ctl,
+                        const Waiter &w, int grid, size_t smem, long long *trace,
+                        cudaStream_t s)
 {
     cudaError_t e = launch_prologue<T>(ctl, s);
-    if (e != cudaSuccess || nmat <= 0) return e;
-    if (trans) {
-        k_batch<T, true><<<grid, kBatchThreads, smem, s>>>(mats, nmat, order, b, x, ctl, w, trace);
-    } else {
-        k_batch<T, false><<<grid, kBatchThreads, smem, s>>>(mats, nmat, order, b, x, ctl, w, trace);
-    }
+    if (e != cudaSuccess || nitems <= 0) return e;
+    if (trans)
+        k_batch<T, true><<<grid, kBatchThreads, smem, s>>>(mats, items, nitems, order, b, x, ctl, w, trace);
+    else
+        k_batch<T, false><<<grid, kBatchThreads, smem, s>>>(mats, items, nitems, order, b, x, ctl, w, trace);
     return cudaGetLastError();
 }
 
@@ -203,9 +203,9 @@ cudaError_t batch_tt_apply(const BatchMat *mats, int32_t nmat, const int64_t *ro
 }
 
 #define SPT_INST(T)                                                                              \
-    template cudaError_t batch_solve<T>(const BatchMat *, int32_t, const int32_t *, const T *, T *, \
-                                        bool, PlanCtl *, const Waiter &, int, size_t,            \
-                                        long long *, cudaStream_t);                              \
+    template cudaError_t batch_solve<T>(const BatchMat *, const BatchItem *, int32_t,             \
+                                        const int32_t *, const T *, T *, bool, PlanCtl *,        \
+                                        const Waiter &, int, size_t, long long *, cudaStream_t); \
     template cudaError_t batch_grad_vals<T>(const BatchMat *, int32_t, const int64_t *, int64_t, \
                                             const T *, const T *, T *, cudaStream_t);            \
     template cudaError_t batch_tt_apply<T>(const BatchMat *, int32_t, const int64_t *, int64_t,  \

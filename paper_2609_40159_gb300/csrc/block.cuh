@@ -263,7 +263,8 @@ __device__ bool block_solve_sweep(const Sys<T> &A, const Rhs<T> &R, int kc, int 
     (void)P;
     const int lane = threadIdx.x & 31;
     const int n = A.n;
-    const int ring = kc * 32;
+    const int ring = kc * 32;  // a power of two
+    const int rmask = ring - 1;
     const int nchunks = (n + 31) / 32;
     const int kt = R.k;
     const int wid = threadIdx.x >> 5;
@@ -332,20 +333,27 @@ __device__ bool block_solve_sweep(const Sys<T> &A, const Rhs<T> &R, int kc, int 
         if (!__all_sync(SPT_FULL_MASK, ok)) return false;
         // ---- earlier groups (ring) and this group (dmask + coef table;
         // unused entries write row 31, which the sweep never reads)
+        // (ring loads first, then the coefficient stores, so that the loads
+        // need not wait behind stores they might alias)
         unsigned dmask = 0;
         bool any_old = false;
 #pragma unroll
         for (int u = 0; u < kPreload; ++u) {
             const bool has = valid && a + u < e;
             const int pj = order_pos<TR>(n, jj[u]);
-            const bool in = has && pj >= base;
             const bool far = has && pj < base;
             const bool old = far && (c - (pj >> 5) >= kc);
             any_old |= old;
             const bool use = far && !old;
+            axpy_vec<T, KT>(use ? vv[u] : T(0), ring0 + (use ? (pj & rmask) * KT : 0), acc);
+        }
+#pragma unroll
+        for (int u = 0; u < kPreload; ++u) {
+            const bool has = valid && a + u < e;
+            const int pj = order_pos<TR>(n, jj[u]);
+            const bool in = has && pj >= base;
             coef[(in ? pj - base : 31) * 32 + lane] = vv[u];
             dmask |= in ? (1u << (pj - base)) : 0u;
-            axpy_vec<T, KT>(use ? vv[u] : T(0), ring0 + (use ? (pj % ring) * KT : 0), acc);
         }
         if (__any_sync(SPT_FULL_MASK, any_old)) {
 #pragma unroll
@@ -368,7 +376,7 @@ __device__ bool block_solve_sweep(const Sys<T> &A, const Rhs<T> &R, int kc, int 
                 dmask |= 1u << (pj - base);
                 coef[(pj - base) * 32 + lane] = v;
             } else if (c - (pj >> 5) < kc) {
-                axpy_vec<T, KT>(v, ring0 + (pj % ring) * KT, acc);
+                axpy_vec<T, KT>(v, ring0 + (pj & rmask) * KT, acc);
             } else {
                 const T *xx = R.x + (int64_t)j * R.ld;
 #pragma unroll
@@ -389,17 +397,19 @@ __device__ bool block_solve_sweep(const Sys<T> &A, const Rhs<T> &R, int kc, int 
             if (KT > 4 && !((need >> s2) & 1u)) continue;  // warp-uniform
             const bool hit = (dmask >> s2) & 1u;
             const T cv = coef[s2 * 32 + lane];
-            const T cfr = hit ? cv * rinv : T(0);
+            const T cfr = cv * rinv;
 #pragma unroll
             for (int r = 0; r < KT; ++r) {
                 const T xs = __shfl_sync(SPT_FULL_MASK, t[r], s2);
+                // a select, not a zero coefficient: an overflowed x_s must
+                // not turn independent rows into NaN
                 t[r] = hit ? t[r] - cfr * xs : t[r];
             }
         }
         // ---- publish: ring values, then the prefix (CTA-scope release),
         // then the global copy (its readers are kc >= nwarps+2 groups later
         // and synchronise through later releases)
-        if (valid) store_vec<T, KT>(const_cast<T *>(sm.xr) + (pos % ring) * KT, t);
+        if (valid) store_vec<T, KT>(const_cast<T *>(sm.xr) + (pos & rmask) * KT, t);
         const bool hold = __any_sync(SPT_FULL_MASK, valid && i == withhold);
         __syncwarp();
         if (lane == 0 && !hold) st_release_cta_smem(prefix, c + 1);

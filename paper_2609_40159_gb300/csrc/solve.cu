@@ -371,6 +371,11 @@ __global__ void __launch_bounds__(kBlockThreads)
 k_block(Sys<T> A, Rhs<T> R, int rpw, int kc, int P, int nwarps, SyncArgs sy)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
+    // one block per tile of KT right-hand-side columns: independent chains
+    const int r0 = blockIdx.x * KT;
+    R.b += r0;
+    R.x += r0;
+    R.k = min(KT, R.k - r0);
     const int ring = kc * rpw;
     BlockSmem<T, KT> sm = carve_block_smem<T, KT>(smraw, ring, kc, nwarps);
     reset_block_smem<T, KT>(sm, ring, kc);
@@ -569,14 +574,17 @@ cudaError_t solve_syncfree(const Sys<T> &A, const Rhs<T> &R, int rpw, int kt, bo
 void block_geometry(int rpw, int kt, bool f64, int nwarps, int *kc, int *P)
 {
     // Throttle distance P (row groups a group may run ahead of the completed
-    // prefix) defaults to the number of active warps plus two; the ring holds
-    // kc = 2P groups.  When that does not fit the shared-memory budget
-    // (many right-hand sides), P shrinks; correctness only needs kc >= 2P.
-    *P = nwarps + 2;
-    while (*P > 2 && block_smem_bytes(rpw, kt, 2 * (*P), f64, nwarps) > kBlockSmemBudget) --(*P);
-    *kc = 2 * (*P);
-    while (*kc < 4096 / rpw && block_smem_bytes(rpw, kt, (*kc) * 2, f64, nwarps) <= kBlockSmemBudget / 2)
-        *kc *= 2;  // a longer ring keeps more dependencies in shared memory
+    // prefix) is about the number of active warps; the ring holds kc >= 2P
+    // groups, kc a power of two (slots are addressed with a mask).  When
+    // that does not fit the shared-memory budget (many right-hand sides) the
+    // ring shrinks; correctness only needs kc >= 2P >= 2.
+    int k = 4;
+    while (k < 2 * (nwarps + 2)) k <<= 1;
+    while (k > 4 && block_smem_bytes(rpw, kt, k, f64, nwarps) > kBlockSmemBudget) k >>= 1;
+    *P = k / 2;
+    while (k < 4096 / rpw && block_smem_bytes(rpw, kt, k * 2, f64, nwarps) <= kBlockSmemBudget / 2)
+        k <<= 1;  // a longer ring keeps more dependencies in shared memory
+    *kc = k;
 }
 
 int block_warps_for(double rows_per_level, int rpw)
@@ -611,26 +619,29 @@ static cudaError_t blk_launch(const Sys<T> &A, const Rhs<T> &R, int rpw, bool tr
     block_geometry(rpw, KT, sizeof(T) == 8, nwarps, &kc, &P);
     const size_t smem = block_smem_bytes(rpw, KT, kc, sizeof(T) == 8, nwarps);
     if (smem > kBlockSmemBudget) return cudaErrorInvalidConfiguration;
+    const int tiles = (R.k + KT - 1) / KT;
     if (trans) {
         raise_smem_once<k_block<T, KT, true>>();
-        k_block<T, KT, true><<<1, kBlockThreads, smem, s>>>(A, R, rpw, kc, P, nwarps, sy);
+        k_block<T, KT, true><<<tiles, kBlockThreads, smem, s>>>(A, R, rpw, kc, P, nwarps, sy);
     } else {
         raise_smem_once<k_block<T, KT, false>>();
-        k_block<T, KT, false><<<1, kBlockThreads, smem, s>>>(A, R, rpw, kc, P, nwarps, sy);
+        k_block<T, KT, false><<<tiles, kBlockThreads, smem, s>>>(A, R, rpw, kc, P, nwarps, sy);
     }
     return cudaGetLastError();
 }
 
+// Columns per thread block: the next power of two up to 8; wider right-hand
+// sides run as several blocks of 8 columns.
 int block_kt_for(int k)
 {
     int kt = 1;
-    while (kt < k) kt <<= 1;
+    while (kt < k && kt < 8) kt <<= 1;
     return kt;
 }
 
 bool block_mode_supported(int k, bool f64)
 {
-    if (k < 1 || k > 32) return false;
+    if (k < 1) return false;
     const int kt = block_kt_for(k);
     int kc, P;
     block_geometry(32, kt, f64, kMaxBlockWarps, &kc, &P);
@@ -648,9 +659,7 @@ cudaError_t solve_block(const Sys<T> &A, const Rhs<T> &R, int rpw, int kt, bool 
     case 1: return blk_launch<T, 1>(A, R, rpw, trans, sy, nwarps, s);
     case 2: return blk_launch<T, 2>(A, R, rpw, trans, sy, nwarps, s);
     case 4: return blk_launch<T, 4>(A, R, rpw, trans, sy, nwarps, s);
-    case 8: return blk_launch<T, 8>(A, R, rpw, trans, sy, nwarps, s);
-    case 16: return blk_launch<T, 16>(A, R, rpw, trans, sy, nwarps, s);
-    default: return blk_launch<T, 32>(A, R, rpw, trans, sy, nwarps, s);
+    default: return blk_launch<T, 8>(A, R, rpw, trans, sy, nwarps, s);
     }
 }
 

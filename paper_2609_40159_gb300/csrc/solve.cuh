@@ -110,12 +110,7 @@ constexpr size_t kBlockSmemBudget = 200 * 1024;
 // Per-matrix descriptor of a batched plan (device resident).
 struct BatchMat {
     int32_t n;
-    int32_t k;        // right-hand sides
-    int32_t rpw;      // rows per warp
-    int32_t kt;       // rhs register tile (>= k)
-    int32_t kc;       // ring row groups (block mode)
-    int32_t P;        // throttle distance in row groups
-    int32_t nw;       // active warps of the thread block
+    int32_t k;        // right-hand sides (leading dimension of its blocks)
     int64_t nnz;
     const int32_t *rp, *ci;
     const void *v;
@@ -128,12 +123,28 @@ struct BatchMat {
     int64_t row_off;   // first global row of the matrix
 };
 
-// One persistent launch: thread blocks take matrices in `order` from the
-// control block's ticket and solve each with the block algorithm.
+// Work item of a batched solve: the columns [r0, r0+kt) of one system's
+// right-hand sides (the columns are independent problems, so a system with
+// many right-hand sides becomes several items solved by different blocks).
+struct BatchItem {
+    int32_t mat;
+    int32_t r0;
+    int32_t kt;       // columns of this item
+    int32_t KT;       // register tile (power of two >= kt)
+    int32_t rpw;      // rows per warp
+    int32_t kc;       // ring row groups (block mode)
+    int32_t P;        // throttle distance in row groups
+    int32_t nw;       // active warps of the thread block
+};
+
+// One persistent launch: thread blocks take work items in `order` from the
+// control block's ticket and solve each with the block algorithm; trace
+// receives (start ns, end ns, SM) per item.
 template <class T>
-cudaError_t batch_solve(const BatchMat *mats, int32_t nmat, const int32_t *order, const T *b,
-                        T *x, bool trans, PlanCtl *ctl, const Waiter &w, int grid,
-                        size_t smem, long long *trace, cudaStream_t s);
+cudaError_t batch_solve(const BatchMat *mats, const BatchItem *items, int32_t nitems,
+                        const int32_t *order, const T *b, T *x, bool trans, PlanCtl *ctl,
+                        const Waiter &w, int grid, size_t smem, long long *trace,
+                        cudaStream_t s);
 // Value gradients of all matrices (row_off: nmat+1 prefix of n, device).
 template <class T>
 cudaError_t batch_grad_vals(const BatchMat *mats, int32_t nmat, const int64_t *row_off,

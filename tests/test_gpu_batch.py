@@ -56,6 +56,30 @@ def test_batch_small(dt):
             assert relerr(gv[a:e].cpu().numpy(), gv_ref) <= (1e-12 if dt == np.float64 else 1e-4), m
 
 
+@pytest.mark.parametrize("tile", [1, 2, 4, 8, "mixed"])
+def test_batch_rhs_tiles(tile):
+    """Every column tile width, and a different width per system: systems
+    split into independent work items of at most `tile` columns, ragged last
+    tiles included (nrhs up to 32)."""
+    items = S.batch_spec(nmat=24, seed=29, n_lo=300, n_hi=6000, dtype=np.float64)
+    P, plan, b, refs = _build(items, np.float64)
+    tiles = [(1, 2, 4, 8)[m % 4] for m in range(len(items))] if tile == "mixed" else tile
+    rpw = [(32, 16, 8, 4, 1)[m % 5] for m in range(len(items))] if tile == "mixed" else None
+    plan.set_geometry(rows_per_warp=rpw, rhs_tile=tiles)
+    x = plan.solve(b)
+    w = torch.randn_like(b)
+    gb = plan.solve_transpose(w)
+    assert P.handle().status() == 0
+    for m, it in enumerate(items):
+        x_ref = oracle.solve(widened(refs[m]), it.b)
+        assert relerr(plan.unpack(x, m).cpu().numpy(), x_ref) <= TOL[np.float64], m
+        if not it.rewritten:
+            g_ref = oracle.solve_transpose(widened(refs[m]), plan.unpack(w, m).cpu().numpy())
+            assert relerr(plan.unpack(gb, m).cpu().numpy(), g_ref) <= TOL[np.float64], m
+    with pytest.raises(P.SpTRSVError):
+        plan.set_geometry(rhs_tile=3)
+
+
 def test_batch_graph_replay_and_loop_equivalence():
     import paper_2609_40159_gb300 as P
     items = S.batch_spec(nmat=24, seed=17, n_lo=500, n_hi=8000, dtype=np.float32)
