@@ -117,20 +117,34 @@ def batch_classes(bplan: BatchPlan):
 
 def tune_batch(bplan: BatchPlan, b: torch.Tensor, candidates=(8, 16, 32), tiles=(2, 4, 8), reps=3,
                rounds=1):
-    """Per size class rows-per-warp and right-hand-side tile of the batched
-    solve (coordinate descent: each class tries every candidate of one knob
-    with everything else fixed)."""
+    """Rows-per-warp and right-hand-side tile of the batched solve.  The
+    batch time is a makespan, so the search first sets one tile width for
+    every system, then refines per size class (coordinate descent: each
+    class tries every candidate of one knob with everything else fixed).
+    A rows-per-warp of 0 keeps the plan's default for that system."""
     labels = batch_classes(bplan)
     classes = sorted(set(labels))
-    choice = {c: [32, 8] for c in classes}
     x = torch.empty_like(b)
+    log = []
 
-    def apply():
+    def apply(choice):
         bplan.set_geometry([choice[l][0] for l in labels], [choice[l][1] for l in labels])
 
-    apply()
-    best_ms = time_call(lambda: bplan.solve(b, out=x), reps=reps)
-    log = [dict(step="start", ms=best_ms)]
+    def measure(choice):
+        try:
+            apply(choice)
+        except L.SpTRSVError:
+            return None
+        return time_call(lambda: bplan.solve(b, out=x), reps=reps)
+
+    best, best_ms = None, float("inf")
+    for t in tiles:
+        choice = {c: [0, t] for c in classes}
+        ms = measure(choice)
+        log.append(dict(step="uniform", rhs_tile=t, ms=ms))
+        if ms is not None and ms < best_ms:
+            best, best_ms = choice, ms
+    choice = best
     for _ in range(rounds):
         for c in classes:
             for knob, cands in ((0, candidates), (1, tiles)):
@@ -139,15 +153,11 @@ def tune_batch(bplan: BatchPlan, b: torch.Tensor, candidates=(8, 16, 32), tiles=
                     if cand == keep:
                         continue
                     choice[c][knob] = cand
-                    try:
-                        apply()
-                    except L.SpTRSVError:
-                        continue
-                    ms = time_call(lambda: bplan.solve(b, out=x), reps=reps)
+                    ms = measure(choice)
                     log.append(dict(cls=c, knob=("rows_per_warp", "rhs_tile")[knob], value=cand, ms=ms))
-                    if ms < best_ms * 0.995:
+                    if ms is not None and ms < best_ms * 0.995:
                         best_ms, keep = ms, cand
                 choice[c][knob] = keep
-                apply()
+    apply(choice)
     return dict(choice={c: dict(rows_per_warp=v[0], rhs_tile=v[1]) for c, v in choice.items()}, ms=best_ms,
                 log=log)

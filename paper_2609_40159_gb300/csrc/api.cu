@@ -111,7 +111,8 @@ struct sptrsv_plan_st {
     BatchItem *d_items = nullptr;        // work items: (system, rhs column tile) and its geometry
     int32_t nitems = 0, max_items = 0;
     int32_t *d_order = nullptr;
-    int64_t *d_row_off = nullptr;
+    RowChunk *d_gchunks = nullptr, *d_tchunks = nullptr;  // all 32-row chunks; chunks with T rows
+    int64_t n_gchunks = 0, n_tchunks = 0;
     long long *d_trace = nullptr;  // per work item: start ns, end ns, SM of the last batch solve
     size_t batch_smem = 0;
     int batch_grid_sz = 0;
@@ -510,7 +511,7 @@ extern "C" sptrsv_status sptrsv_plan_info(sptrsv_plan p, int32_t *nlevels, int32
     }
     if (mode) *mode = p->batched ? SPTRSV_MODE_BLOCK : p->mode;
     if (rows_per_warp) *rows_per_warp = p->batched ? (p->b_rpw.empty() ? 32 : p->b_rpw[0]) : p->rpw;
-    if (rhs_tile) *rhs_tile = p->batched ? (p->b_tile.empty() ? 8 : p->b_tile[0]) : p->kt;
+    if (rhs_tile) *rhs_tile = p->batched ? (p->b_tile.empty() ? 4 : p->b_tile[0]) : p->kt;
     return SPTRSV_OK;
 }
 
@@ -609,8 +610,9 @@ sptrsv_status rebuild_items(sptrsv_plan p)
             I.kt = std::min(tile, k - r0);
             I.KT = pow2_at_least(I.kt);
             I.rpw = p->b_rpw[m];
-            I.nw = block_warps_for(M.nlevels > 0 ? (double)M.L.n / M.nlevels : 1.0, I.rpw);
-            block_geometry(I.rpw, I.KT, f64, I.nw, &I.kc, &I.P);
+            I.nw = std::min(kBatchWarps,
+                            block_warps_for(M.nlevels > 0 ? (double)M.L.n / M.nlevels : 1.0, I.rpw));
+            block_geometry(I.rpw, I.KT, f64, I.nw, &I.kc, &I.P, kBatchSmemGrow);
             smem = std::max(smem, block_smem_bytes(I.rpw, I.KT, I.kc, f64, I.nw));
             items.push_back(I);
             // chain of n / 32 row groups whose cost grows with the tile width,
@@ -661,7 +663,7 @@ extern "C" sptrsv_status sptrsv_batch_plan_create(sptrsv_handle h, int32_t nmat,
     p->row_off.assign((size_t)nmat + 1, 0);
     p->h_mats.resize((size_t)nmat);
     p->b_rpw.assign((size_t)nmat, 32);
-    p->b_tile.assign((size_t)nmat, 8);
+    p->b_tile.assign((size_t)nmat, 4);
     int64_t ktot = 0;
     for (int m = 0; m < nmat; ++m) {
         sptrsv_status st = check_csr(&Ls[m]);
@@ -698,13 +700,36 @@ extern "C" sptrsv_status sptrsv_batch_plan_create(sptrsv_handle h, int32_t nmat,
     e = p->alloc(&p->d_mats, sizeof(BatchMat) * (size_t)(nmat > 0 ? nmat : 1));
     if (e == cudaSuccess) e = p->alloc(&p->d_items, sizeof(BatchItem) * (size_t)p->max_items);
     if (e == cudaSuccess) e = p->alloc(&p->d_order, sizeof(int32_t) * (size_t)p->max_items);
-    if (e == cudaSuccess) e = p->alloc(&p->d_row_off, sizeof(int64_t) * ((size_t)nmat + 1));
     if (e == cudaSuccess) e = p->alloc(&p->d_trace, sizeof(long long) * 3 * (size_t)p->max_items);
     if (e == cudaSuccess && nmat > 0)
         e = cudaMemcpy(p->d_mats, p->h_mats.data(), sizeof(BatchMat) * nmat, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess)
-        e = cudaMemcpy(p->d_row_off, p->row_off.data(), sizeof(int64_t) * (nmat + 1), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) { sptrsv_plan_destroy(p); return from_cuda(e); }
+    {
+        // chunk tables of the elementwise adjoint kernels: every 32-row chunk,
+        // and the chunks whose T-row mask word is non-zero
+        std::vector<RowChunk> g, t;
+        std::vector<uint32_t> mask;
+        e = cudaStreamSynchronize(p->h->stream);  // T-row masks are built on the handle's stream
+        for (int m = 0; m < nmat && e == cudaSuccess; ++m) {
+            const PlanMat &M = p->mats[m];
+            const int32_t nw = (M.L.n + 31) / 32;
+            for (int32_t c = 0; c < nw; ++c) g.push_back(RowChunk{m, 32 * c});
+            if (!M.hasT || nw == 0) continue;
+            mask.resize((size_t)nw);
+            e = cudaMemcpy(mask.data(), M.d_tmask, sizeof(uint32_t) * nw, cudaMemcpyDeviceToHost);
+            for (int32_t c = 0; c < nw && e == cudaSuccess; ++c)
+                if (mask[c]) t.push_back(RowChunk{m, 32 * c});
+        }
+        p->n_gchunks = (int64_t)g.size();
+        p->n_tchunks = (int64_t)t.size();
+        if (e == cudaSuccess) e = p->alloc(&p->d_gchunks, sizeof(RowChunk) * std::max<size_t>(g.size(), 1));
+        if (e == cudaSuccess) e = p->alloc(&p->d_tchunks, sizeof(RowChunk) * std::max<size_t>(t.size(), 1));
+        if (e == cudaSuccess && !g.empty())
+            e = cudaMemcpy(p->d_gchunks, g.data(), sizeof(RowChunk) * g.size(), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && !t.empty())
+            e = cudaMemcpy(p->d_tchunks, t.data(), sizeof(RowChunk) * t.size(), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) { sptrsv_plan_destroy(p); return from_cuda(e); }
+    }
     sptrsv_status st = rebuild_items(p);
     if (st != SPTRSV_OK) { sptrsv_plan_destroy(p); return st; }
     *plan = p;
@@ -810,11 +835,11 @@ extern "C" sptrsv_status sptrsv_batch_grad_vals(sptrsv_plan p, const void *gb, c
     if (!gb || !x || !gvals) return SPTRSV_EINVAL;
     cudaError_t e;
     if (p->dtype == SPTRSV_F64)
-        e = batch_grad_vals<double>(p->d_mats, nmat, p->d_row_off, p->row_off[nmat], (const double *)gb,
-                                    (const double *)x, (double *)gvals, p->h->stream);
+        e = batch_grad_vals<double>(p->d_mats, p->d_gchunks, p->n_gchunks, (const double *)gb, (const double *)x,
+                                    (double *)gvals, p->h->stream);
     else
-        e = batch_grad_vals<float>(p->d_mats, nmat, p->d_row_off, p->row_off[nmat], (const float *)gb,
-                                   (const float *)x, (float *)gvals, p->h->stream);
+        e = batch_grad_vals<float>(p->d_mats, p->d_gchunks, p->n_gchunks, (const float *)gb, (const float *)x,
+                                   (float *)gvals, p->h->stream);
     return from_cuda(e);
 }
 
@@ -826,10 +851,10 @@ extern "C" sptrsv_status sptrsv_batch_tt_apply(sptrsv_plan p, const void *gbp, v
     if (!gbp || !gb) return SPTRSV_EINVAL;
     cudaError_t e;
     if (p->dtype == SPTRSV_F64)
-        e = batch_tt_apply<double>(p->d_mats, nmat, p->d_row_off, p->row_off[nmat], p->rhs_off[nmat],
-                                   (const double *)gbp, (double *)gb, p->h->stream);
+        e = batch_tt_apply<double>(p->d_mats, p->d_tchunks, p->n_tchunks, p->rhs_off[nmat], (const double *)gbp,
+                                   (double *)gb, p->h->stream);
     else
-        e = batch_tt_apply<float>(p->d_mats, nmat, p->d_row_off, p->row_off[nmat], p->rhs_off[nmat],
-                                  (const float *)gbp, (float *)gb, p->h->stream);
+        e = batch_tt_apply<float>(p->d_mats, p->d_tchunks, p->n_tchunks, p->rhs_off[nmat], (const float *)gbp,
+                                  (float *)gb, p->h->stream);
     return from_cuda(e);
 }

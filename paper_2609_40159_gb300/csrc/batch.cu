@@ -1,15 +1,17 @@
 // Batched solve: many independent lower-triangular systems of uneven size,
 // each with its own number of right-hand sides, in ONE persistent launch.
-// Thread blocks take whole systems from a ticket (largest estimated critical
-// path first) and run the block algorithm on them; no host work per system,
-// so a batch solve is two kernel nodes in a CUDA graph.
+// Thread blocks take work items -- one system and a tile of at most 8 of its
+// right-hand-side columns -- from a ticket (longest estimated chain first)
+// and run the block algorithm on them; no host work per system, so a batch
+// solve is two kernel nodes in a CUDA graph.  The adjoint's elementwise
+// parts (value gradient, T^T) walk plan-time tables of 32-row chunks.
 #include "block.cuh"
 
 namespace spt {
 
 namespace {
 
-constexpr int kBatchThreads = 32 * kMaxBlockWarps;
+constexpr int kBatchThreads = 32 * kBatchWarps;
 
 template <class T>
 __device__ __forceinline__ Sys<T> sys_of(const BatchMat &M)
@@ -35,7 +37,10 @@ __device__ __forceinline__ bool run_one(const BatchMat &M, const BatchItem &I, u
     R.x = x + M.rhs_off + I.r0;
     R.ld = M.k;
     R.k = I.kt;
-    return block_solve_any<T, KT, TR>(sys_of<T>(M), R, I.rpw, I.kc, I.P, I.nw, sm, w, -1);
+    const bool ok = block_solve_any<T, KT, TR, false>(sys_of<T>(M), R, I.rpw, I.kc, I.P, I.nw, sm, w, -1);
+    __syncthreads();
+    release_block_smem<T, KT>(sm, I.kc);
+    return ok;
 }
 
 __device__ __forceinline__ unsigned sm_id()
@@ -46,7 +51,7 @@ __device__ __forceinline__ unsigned sm_id()
 }
 
 template <class T, bool TR>
-__global__ void __launch_bounds__(kBatchThreads)
+__global__ void __launch_bounds__(kBatchThreads, kBatchMinBlocks)
 k_batch(const BatchMat *__restrict__ mats, const BatchItem *__restrict__ items, int32_t nitems,
         const int32_t *__restrict__ order, const T *b, T *x, PlanCtl *ctl, Waiter w,
         long long *trace)
@@ -81,69 +86,91 @@ k_batch(const BatchMat *__restrict__ mats, const BatchItem *__restrict__ items, 
     }
 }
 
-// Global row r -> matrix index (row_off is the nmat+1 prefix of n).
-__device__ __forceinline__ int mat_of_row(const int64_t *row_off, int nmat, int64_t r)
+// Row of nonzero p inside a 32-row chunk whose lanes hold the chunk's row
+// starts (s = row_ptr[r0 + lane], lanes >= nrows unused): the last lane l <
+// nrows with s_l <= p, by a five-step binary search over the lanes.
+__device__ __forceinline__ int row_in_chunk(int s, int nrows, int p)
 {
-    int lo = 0, hi = nmat - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (row_off[mid] <= r) lo = mid; else hi = mid - 1;
+    int lo = 0;
+#pragma unroll
+    for (int step = 16; step >= 1; step >>= 1) {
+        const int cand = lo + step;
+        const int v = __shfl_sync(SPT_FULL_MASK, s, cand & 31);
+        if (cand < nrows && v <= p) lo = cand;
     }
     return lo;
 }
 
+// dL/dL_ij = -g_b[i,:] . x[j,:] on L's pattern.  One warp per 32-row chunk;
+// the chunk's nonzeros are contiguous in CSR order and are taken 32 at a
+// time, one per lane (coalesced column indices and gradient stores).
 template <class T>
-__global__ void k_batch_grad(const BatchMat *__restrict__ mats, int32_t nmat,
-                             const int64_t *__restrict__ row_off, int64_t total_rows,
-                             const T *__restrict__ gb, const T *__restrict__ x, T *__restrict__ gv)
+__global__ void k_batch_grad(const BatchMat *__restrict__ mats, const RowChunk *__restrict__ chunks,
+                             int64_t nchunks, const T *__restrict__ gb, const T *__restrict__ x,
+                             T *__restrict__ gv)
 {
     const int lane = threadIdx.x & 31;
-    const int g = lane >> 3, sl = lane & 7;  // 4 rows per warp, 8 lanes per row
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t r4 = gw * 4; r4 < total_rows; r4 += nw * 4) {
-        const int64_t r = r4 + g;
-        if (r >= total_rows) continue;
-        const int m = mat_of_row(row_off, nmat, r);
-        const BatchMat &M = mats[m];
-        const int i = (int)(r - row_off[m]);
+    for (int64_t c = gw; c < nchunks; c += nw) {
+        const RowChunk ch = chunks[c];
+        const BatchMat &M = mats[ch.mat];
+        const int nrows = min(32, M.n - ch.r0);
         const int k = M.k;
-        const int a = ldro(M.rp + i), e = ldro(M.rp + i + 1);
-        const T *gi = gb + M.rhs_off + (int64_t)i * k;
+        const int s = ldro(M.rp + ch.r0 + min(lane, nrows));
+        const int pe = __shfl_sync(SPT_FULL_MASK, s, nrows & 31);
+        const int end = nrows == 32 ? ldro(M.rp + ch.r0 + 32) : pe;
+        const int p0 = __shfl_sync(SPT_FULL_MASK, s, 0);
         const T *xb = x + M.rhs_off;
+        const T *gbb = gb + M.rhs_off;
         T *out = gv + M.vals_off;
-        for (int p = a + sl; p < e; p += 8) {
-            const T *xj = xb + (int64_t)ldro(M.ci + p) * k;
-            T s = T(0);
-            for (int q = 0; q < k; ++q) s += gi[q] * xj[q];
-            out[p] = -s;
+        for (int base = p0; base < end; base += 32) {
+            const int p = base + lane;
+            const int r = row_in_chunk(s, nrows, p);
+            if (p < end) {
+                const T *gi = gbb + (int64_t)(ch.r0 + r) * k;
+                const T *xj = xb + (int64_t)ldro(M.ci + p) * k;
+                T acc = T(0);
+                for (int q = 0; q < k; ++q) acc += gi[q] * xj[q];
+                out[p] = -acc;
+            }
         }
     }
 }
 
+// g_b += T^T g_b' for the rewritten rows: one warp per 32-row chunk that
+// holds at least one row of T (its T-row mask word is non-zero).
 template <class T>
-__global__ void k_batch_tt(const BatchMat *__restrict__ mats, int32_t nmat,
-                           const int64_t *__restrict__ row_off, int64_t total_rows,
-                           const T *__restrict__ gbp, T *gb)
+__global__ void k_batch_tt(const BatchMat *__restrict__ mats, const RowChunk *__restrict__ chunks,
+                           int64_t nchunks, const T *__restrict__ gbp, T *gb)
 {
     const int lane = threadIdx.x & 31;
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t r = gw; r < total_rows; r += nw) {
-        const int m = mat_of_row(row_off, nmat, r);
-        const BatchMat &M = mats[m];
-        if (M.tmask == nullptr) continue;
-        const int i = (int)(r - row_off[m]);
-        if (!((M.tmask[i >> 5] >> (i & 31)) & 1u)) continue;
+    for (int64_t c = gw; c < nchunks; c += nw) {
+        const RowChunk ch = chunks[c];
+        const BatchMat &M = mats[ch.mat];
         const int k = M.k;
         const T *tv = (const T *)M.tv;
-        for (int p = M.trp[i] + lane; p < M.trp[i + 1]; p += 32) {
-            const T c = tv[p];
-            const int64_t j = M.tci[p];
-            for (int q = 0; q < k; ++q)
-                atomicAdd(gb + M.rhs_off + j * k + q, c * gbp[M.rhs_off + (int64_t)i * k + q]);
+        unsigned word = M.tmask[ch.r0 >> 5];
+        while (word) {
+            const int i = ch.r0 + __ffs(word) - 1;
+            word &= word - 1;
+            const T *gi = gbp + M.rhs_off + (int64_t)i * k;
+            for (int p = ldro(M.trp + i) + lane; p < ldro(M.trp + i + 1); p += 32) {
+                const T cv = ldro(tv + p);
+                T *gj = gb + M.rhs_off + (int64_t)ldro(M.tci + p) * k;
+                for (int q = 0; q < k; ++q) atomicAdd(gj + q, cv * gi[q]);
+            }
         }
     }
+}
+
+int elementwise_grid(int64_t nchunks)
+{
+    // 8 warps per block; grid-stride over the chunks
+    int64_t blocks = (nchunks + 7) / 8;
+    return (int)std::min<int64_t>(std::max<int64_t>(blocks, 1), 152 * 16);
 }
 
 }  // namespace
@@ -179,26 +206,21 @@ cudaError_t batch_solve(const BatchMat *mats, const BatchItem *items, int32_t ni
 }
 
 template <class T>
-cudaError_t batch_grad_vals(const BatchMat *mats, int32_t nmat, const int64_t *row_off,
-                            int64_t total_rows, const T *gb, const T *x, T *gv, cudaStream_t s)
+cudaError_t batch_grad_vals(const BatchMat *mats, const RowChunk *chunks, int64_t nchunks, const T *gb,
+                            const T *x, T *gv, cudaStream_t s)
 {
-    if (total_rows <= 0) return cudaSuccess;
-    int64_t blocks = (total_rows + 31) / 32;
-    if (blocks > 65535 * 4) blocks = 65535 * 4;
-    k_batch_grad<T><<<(int)blocks, 256, 0, s>>>(mats, nmat, row_off, total_rows, gb, x, gv);
+    if (nchunks <= 0) return cudaSuccess;
+    k_batch_grad<T><<<elementwise_grid(nchunks), 256, 0, s>>>(mats, chunks, nchunks, gb, x, gv);
     return cudaGetLastError();
 }
 
 template <class T>
-cudaError_t batch_tt_apply(const BatchMat *mats, int32_t nmat, const int64_t *row_off,
-                           int64_t total_rows, int64_t total_rhs, const T *gbp, T *gb,
-                           cudaStream_t s)
+cudaError_t batch_tt_apply(const BatchMat *mats, const RowChunk *tchunks, int64_t ntchunks,
+                           int64_t total_rhs, const T *gbp, T *gb, cudaStream_t s)
 {
     cudaError_t e = cudaMemcpyAsync(gb, gbp, sizeof(T) * (size_t)total_rhs, cudaMemcpyDeviceToDevice, s);
-    if (e != cudaSuccess || total_rows <= 0) return e;
-    int64_t blocks = (total_rows + 7) / 8;
-    if (blocks > 65535 * 4) blocks = 65535 * 4;
-    k_batch_tt<T><<<(int)blocks, 256, 0, s>>>(mats, nmat, row_off, total_rows, gbp, gb);
+    if (e != cudaSuccess || ntchunks <= 0) return e;
+    k_batch_tt<T><<<elementwise_grid(ntchunks), 256, 0, s>>>(mats, tchunks, ntchunks, gbp, gb);
     return cudaGetLastError();
 }
 
@@ -206,10 +228,10 @@ cudaError_t batch_tt_apply(const BatchMat *mats, int32_t nmat, const int64_t *ro
     template cudaError_t batch_solve<T>(const BatchMat *, const BatchItem *, int32_t,             \
                                         const int32_t *, const T *, T *, bool, PlanCtl *,        \
                                         const Waiter &, int, size_t, long long *, cudaStream_t); \
-    template cudaError_t batch_grad_vals<T>(const BatchMat *, int32_t, const int64_t *, int64_t, \
+    template cudaError_t batch_grad_vals<T>(const BatchMat *, const RowChunk *, int64_t,         \
                                             const T *, const T *, T *, cudaStream_t);            \
-    template cudaError_t batch_tt_apply<T>(const BatchMat *, int32_t, const int64_t *, int64_t,  \
-                                           int64_t, const T *, T *, cudaStream_t);
+    template cudaError_t batch_tt_apply<T>(const BatchMat *, const RowChunk *, int64_t, int64_t, \
+                                           const T *, T *, cudaStream_t);
 SPT_INST(double)
 SPT_INST(float)
 #undef SPT_INST

@@ -8,8 +8,11 @@ namespace spt {
 
 // Shared-memory layout (dynamic): ring of `ring` rows x KT solution values,
 // ring of row tags (position of the row held by the slot, -1 = empty),
-// ring of chunk tags, and counters {ticket, completed prefix}.
+// ring of chunk tags, counters {ticket, completed prefix}; the one-lane-
+// per-row path orders its groups with kc shared mbarriers instead of the
+// tags and the prefix.
 template <class T, int KT> struct BlockSmem {
+    uint64_t *bar;  // kc phase barriers: bar[c % kc] completes when group c-1 is done
     volatile T *xr;
     T *coef;   // per active warp: [32][32] in-group coefficients
     T *xbuf;   // per active warp: KT broadcast values
@@ -231,36 +234,72 @@ __device__ __forceinline__ bool ring_dep(const BlockSmem<T, KT> &sm, const Rhs<T
     return true;
 }
 
-// Block-mode solve with one lane per row (groups of 32 rows).  Groups
-// complete in order: group c waits (one CTA-scope acquire poll by lane 0)
-// until the completed prefix reaches c, applies its dependencies on earlier
-// groups (shared-memory ring for the last kc-1 groups, global memory before
-// that), resolves the dependencies inside the group by the column sweep and
-// publishes prefix = c+1 with a CTA-scope release.  The other warps of the
-// block meanwhile load their next group's metadata and entries, so the
-// loads overlap the chain.  Ring slot safety: a slot of group cj is
-// rewritten by group cj + kc only after the prefix passed cj + kc, i.e. after
-// every reader of cj (groups < cj + kc) has finished.
-// Block-mode solve with one lane per row (groups of 32 rows).  Groups
-// complete in order: group c waits until the completed prefix reaches c
-// (every lane polls the same shared word, so the warp never diverges around
-// the wait), applies its dependencies on earlier groups (shared-memory ring
-// for the last kc-1 groups, global memory before that), resolves the
-// dependencies inside the group by the column sweep and publishes
-// prefix = c+1 with a CTA-scope release.  The other warps of the block
-// meanwhile load their own next group's metadata and entries.  The chain
-// from one group's release to the next group's release contains no
-// lane-divergent control flow (reconverging a divergent warp costs
-// thousands of cycles on this path): loads use clamped, always-valid
-// indices, stores of unused lanes go to a row of the coefficient table that
-// is never read, selections are arithmetic.  Ring slot safety: a slot of
-// group cj is rewritten by group cj + kc only after the prefix passed
-// cj + kc, i.e. after every reader of cj (groups < cj + kc) has finished.
-template <class T, int KT, bool TR>
+// In-group dependencies of a 32-row group, solved in registers.  Lane L
+// holds the scaled candidates t_L = (b_L - sum over earlier groups) / L_LL,
+// coef[s * 32 + L] = L_Ls / L_LL for every in-group dependency s < L (bit s
+// of dmask; other entries of the table are not initialised) and the final
+// x_L = t_L - sum_s coef[s * 32 + L] x_s: 31 steps; step s broadcasts x_s
+// (final once every s' < s was applied) and every lane that depends on row
+// s subtracts its share.
+template <class T, int KT>
+__device__ __forceinline__ void sweep_scalar(T (&t)[KT], unsigned dmask, const T *coef, int lane)
+{
+    const unsigned need = __reduce_or_sync(SPT_FULL_MASK, dmask);
+#pragma unroll
+    for (int s = 0; s < 31; ++s) {
+        // warp-uniform skip of rows nobody depends on; only for wide tiles,
+        // where the step costs more than the branch (a branch stops the
+        // coefficient load from being hoisted onto the previous step)
+        if (KT > 4 && !((need >> s) & 1u)) continue;
+        const bool hit = (dmask >> s) & 1u;
+        const T cf = coef[s * 32 + lane];
+#pragma unroll
+        for (int r = 0; r < KT; ++r) {
+            const T xs = __shfl_sync(SPT_FULL_MASK, t[r], s);
+            // a select, not a zero coefficient: an overflowed x_s must not
+            // turn independent rows into NaN
+            t[r] = hit ? fma(-cf, xs, t[r]) : t[r];
+        }
+    }
+}
+
+// Block-mode solve with one lane per row (groups of 32 rows, dealt to the
+// warps round-robin).  Groups complete in order.  Group c:
+//   1. before any wait: loads its rows' metadata, right-hand sides and first
+//      kPreload entries, builds its in-group coefficient table and applies
+//      the entries older than the shared-memory ring (global memory);
+//   2. waits, then applies the dependencies held in the ring;
+//   3. resolves the in-group dependencies (column sweep) and publishes: ring
+//      values, completion (release), global copy.
+// Single-phase (the batched solve, many blocks per SM): step 2 waits for
+// every group < c on the completed-group counter, which every lane of the
+// warp polls.  Two-phase (TWO, one block on an SM): step 2 waits for the
+// groups <= c-2 only and applies their entries while group c-1 is still
+// being solved; a second wait for group c-1 and its entries precede step 3.
+// Two-phase completion goes through kc shared mbarriers of one arrival
+// each: group g arrives (release) on bar[g % kc], completing that barrier's
+// phase g / kc; a waiting warp is suspended by the hardware instead of
+// polling.  A barrier's next completion (group g + kc) cannot come before
+// the waiters of g (groups g + 1 and g + 2) are done, as kc >= 4.
+// The chain from one completion to the next has no lane-divergent control
+// flow (reconverging a divergent warp costs thousands of cycles on this
+// path): loads use clamped, always-valid indices, stores of unused lanes go
+// to a row of the coefficient table that is never read, selections are
+// arithmetic.
+// Ring slot safety: the slot of group cj is rewritten by group cj + kc only
+// after every group < cj + kc is complete, i.e. after every reader of cj
+// finished.  Global reads: the warp that solved group g stores g's global x
+// (after publishing g) before it publishes its next group, g + nwarps.  A
+// warp starting group c has itself completed c - nwarps, after acquiring
+// the completion of every group < c - nwarps, which covers the global x of
+// every group <= c - 2 nwarps - 1; entries at least kc >= 2 nwarps + 1
+// groups back are therefore read from global memory before the warp waits.
+template <class T, int KT, bool TR, bool TWO>
 __device__ bool block_solve_sweep(const Sys<T> &A, const Rhs<T> &R, int kc, int P, int nwarps,
                                   const BlockSmem<T, KT> &sm, const Waiter &w, int withhold)
 {
     (void)P;
+    constexpr int NP = kPreload;
     const int lane = threadIdx.x & 31;
     const int n = A.n;
     const int ring = kc * 32;  // a power of two
@@ -269,13 +308,9 @@ __device__ bool block_solve_sweep(const Sys<T> &A, const Rhs<T> &R, int kc, int 
     const int kt = R.k;
     const int wid = threadIdx.x >> 5;
     T *coef = sm.coef + (size_t)wid * 1024;
-    int *prefix = sm.ctr + 1;
     const T *ring0 = const_cast<const T *>(sm.xr);
-    for (;;) {
-        int c = 0;
-        if (lane == 0) c = atomicAdd(sm.ctr, 1);
-        c = __shfl_sync(SPT_FULL_MASK, c, 0);
-        if (c >= nchunks) return true;
+    // groups are dealt round-robin: warp w solves w, w + nwarps, ...
+    for (int c = wid; c < nchunks; c += nwarps) {
         const int base = c * 32;
         const int pos = base + lane;
         const bool valid = pos < n;
@@ -285,9 +320,7 @@ __device__ bool block_solve_sweep(const Sys<T> &A, const Rhs<T> &R, int kc, int 
             const int pn = min(pos + 32 * (nwarps + 1), n - 1);
             prefetch_row<T, TR>(A, TR ? n - 1 - pn : pn);
         }
-        // ---- independent of the solution: metadata, right-hand side and
-        // the first kPreload entries (clamped to the row's diagonal entry),
-        // all complete before this group's turn
+        // ---- 1. independent of the solution
         const int a = RV<T, TR>::beg(A, i);
         const int e = RV<T, TR>::end(A, i);
         const int safe = TR ? a - 1 : e;  // position of the diagonal entry
@@ -307,130 +340,149 @@ __device__ bool block_solve_sweep(const Sys<T> &A, const Rhs<T> &R, int kc, int 
                     if (r < kt) acc[r] -= tv * bb[r];
             }
         }
-        int jj[kPreload];
-        T vv[kPreload];
+        int jj[NP];
+        T vv[NP];
 #pragma unroll
-        for (int u = 0; u < kPreload; ++u) {
+        for (int u = 0; u < NP; ++u) {
             const int q = a + u < e ? a + u : safe;
-            jj[u] = RV<T, TR>::col(A, q);
+            jj[u] = order_pos<TR>(n, RV<T, TR>::col(A, q));
             vv[u] = RV<T, TR>::val(A, q);
         }
-        consume(rinv);
+        unsigned dmask = 0;
 #pragma unroll
-        for (int r = 0; r < KT; ++r) consume(bv[r]);
-#pragma unroll
-        for (int u = 0; u < kPreload; ++u) {
-            consume(jj[u]);
-            consume(vv[u]);
+        for (int u = 0; u < NP; ++u) {
+            const bool in = valid && a + u < e && jj[u] >= base;
+            coef[(in ? jj[u] - base : 31) * 32 + lane] = vv[u] * rinv;
+            dmask |= in ? (1u << (jj[u] - base)) : 0u;
         }
-        // ---- wait for every earlier group
+        const bool longrow = valid && e - a > NP;
+        for (int p = a + NP; longrow && p < e; ++p) {
+            const int pj = order_pos<TR>(n, RV<T, TR>::col(A, p));
+            if (pj >= base) {
+                dmask |= 1u << (pj - base);
+                coef[(pj - base) * 32 + lane] = RV<T, TR>::val(A, p) * rinv;
+            }
+        }
+        const bool anylong = __any_sync(SPT_FULL_MASK, longrow);
         bool ok = true;
         {
-            WaitClock clk;
-            while (ld_acquire_cta_smem(prefix) < c)
-                if (clk.expired(w)) { ok = false; break; }
-        }
-        if (!__all_sync(SPT_FULL_MASK, ok)) return false;
-        // ---- earlier groups (ring) and this group (dmask + coef table;
-        // unused entries write row 31, which the sweep never reads)
-        // (ring loads first, then the coefficient stores, so that the loads
-        // need not wait behind stores they might alias)
-        unsigned dmask = 0;
-        bool any_old = false;
+            // entries older than the ring (groups <= c - kc) are read from
+            // global memory now, before the group's turn (see the visibility
+            // argument above)
+            bool any_old = false;
 #pragma unroll
-        for (int u = 0; u < kPreload; ++u) {
-            const bool has = valid && a + u < e;
-            const int pj = order_pos<TR>(n, jj[u]);
-            const bool far = has && pj < base;
-            const bool old = far && (c - (pj >> 5) >= kc);
-            any_old |= old;
-            const bool use = far && !old;
-            axpy_vec<T, KT>(use ? vv[u] : T(0), ring0 + (use ? (pj & rmask) * KT : 0), acc);
-        }
+            for (int u = 0; u < NP; ++u)
+                any_old |= valid && a + u < e && c - (jj[u] >> 5) >= kc;
+            if (__any_sync(SPT_FULL_MASK, any_old)) {
 #pragma unroll
-        for (int u = 0; u < kPreload; ++u) {
-            const bool has = valid && a + u < e;
-            const int pj = order_pos<TR>(n, jj[u]);
-            const bool in = has && pj >= base;
-            coef[(in ? pj - base : 31) * 32 + lane] = vv[u];
-            dmask |= in ? (1u << (pj - base)) : 0u;
-        }
-        if (__any_sync(SPT_FULL_MASK, any_old)) {
+                for (int u = 0; u < NP; ++u) {
+                    if (valid && a + u < e && c - (jj[u] >> 5) >= kc) {
+                        const T *xx = R.x + (int64_t)order_pos<TR>(n, jj[u]) * R.ld;
 #pragma unroll
-            for (int u = 0; u < kPreload; ++u) {
-                const bool has = valid && a + u < e;
-                const int pj = order_pos<TR>(n, jj[u]);
-                if (has && pj < base && c - (pj >> 5) >= kc) {
-                    const T *xx = R.x + (int64_t)jj[u] * R.ld;
+                        for (int r = 0; r < KT; ++r)
+                            if (r < kt) acc[r] += vv[u] * xx[r];
+                    }
+                }
+            }
+            for (int p = a + NP; longrow && p < e; ++p) {
+                const int j = RV<T, TR>::col(A, p);
+                if (c - (order_pos<TR>(n, j) >> 5) >= kc) {
+                    const T v = RV<T, TR>::val(A, p);
+                    const T *xx = R.x + (int64_t)j * R.ld;
 #pragma unroll
                     for (int r = 0; r < KT; ++r)
-                        if (r < kt) acc[r] += vv[u] * xx[r];
+                        if (r < kt) acc[r] += v * xx[r];
                 }
             }
         }
-        for (int p = a + kPreload; valid && p < e; ++p) {  // long rows
-            const int j = RV<T, TR>::col(A, p);
-            const T v = RV<T, TR>::val(A, p);
-            const int pj = order_pos<TR>(n, j);
-            if (pj >= base) {
-                dmask |= 1u << (pj - base);
-                coef[(pj - base) * 32 + lane] = v;
-            } else if (c - (pj >> 5) < kc) {
-                axpy_vec<T, KT>(v, ring0 + (pj & rmask) * KT, acc);
-            } else {
-                const T *xx = R.x + (int64_t)j * R.ld;
+
+        consume(rinv);
 #pragma unroll
-                for (int r = 0; r < KT; ++r)
-                    if (r < kt) acc[r] += v * xx[r];
+        for (int r = 0; r < KT; ++r) consume(bv[r]);
+        // ---- 2. groups <= c-2 (group g's arrival is phase g / kc of
+        // barrier g % kc); single-phase: all earlier groups (the completed-
+        // group counter reaches c; every lane polls it)
+        if constexpr (TWO) {
+            if (c >= 2) ok = mbar_wait(sm.bar + ((c - 2) & (kc - 1)), ((unsigned)(c - 2) / kc) & 1u, w);
+        } else {
+            WaitClock clk;
+            while (ld_acquire_cta_smem(sm.ctr + 1) < c)
+                if (clk.expired(w)) { ok = false; break; }
+        }
+        if (!__all_sync(SPT_FULL_MASK, ok)) return false;
+        const int lim = TWO ? base - 32 : base;  // ring entries below lim are applied now
+#pragma unroll
+        for (int u = 0; u < NP; ++u) {
+            const bool use = valid && a + u < e && jj[u] < lim && c - (jj[u] >> 5) < kc;
+            axpy_vec<T, KT>(use ? vv[u] : T(0), ring0 + (use ? (jj[u] & rmask) * KT : 0), acc);
+        }
+        if (anylong) {
+            for (int p = a + NP; longrow && p < e; ++p) {
+                const int pj = order_pos<TR>(n, RV<T, TR>::col(A, p));
+                if (pj < lim && c - (pj >> 5) < kc)
+                    axpy_vec<T, KT>(RV<T, TR>::val(A, p), ring0 + (pj & rmask) * KT, acc);
+            }
+        }
+        // ---- 3. group c-1 (two-phase), then this group
+        if constexpr (TWO) {
+            if (c >= 1) ok = mbar_wait(sm.bar + ((c - 1) & (kc - 1)), ((unsigned)(c - 1) / kc) & 1u, w);
+            if (!__all_sync(SPT_FULL_MASK, ok)) return false;
+#pragma unroll
+            for (int u = 0; u < NP; ++u) {
+                const bool prev = valid && a + u < e && jj[u] < base && jj[u] >= base - 32;
+                axpy_vec<T, KT>(prev ? vv[u] : T(0), ring0 + (prev ? (jj[u] & rmask) * KT : 0), acc);
+            }
+            if (anylong) {
+                for (int p = a + NP; longrow && p < e; ++p) {
+                    const int pj = order_pos<TR>(n, RV<T, TR>::col(A, p));
+                    if (pj < base && pj >= base - 32)
+                        axpy_vec<T, KT>(RV<T, TR>::val(A, p), ring0 + (pj & rmask) * KT, acc);
+                }
             }
         }
         __syncwarp();
-        // ---- in-group dependencies: unrolled column sweep on the scaled
-        // candidates t = (b - acc) / L_ii; a dependency on row s is one
-        // t -= (coef / L_ii) * x_s after x_s's shuffle broadcast
         T t[KT];
 #pragma unroll
         for (int r = 0; r < KT; ++r) t[r] = (bv[r] - acc[r]) * rinv;
-        const unsigned need = __reduce_or_sync(SPT_FULL_MASK, dmask);
-#pragma unroll
-        for (int s2 = 0; s2 < 31; ++s2) {
-            if (KT > 4 && !((need >> s2) & 1u)) continue;  // warp-uniform
-            const bool hit = (dmask >> s2) & 1u;
-            const T cv = coef[s2 * 32 + lane];
-            const T cfr = cv * rinv;
-#pragma unroll
-            for (int r = 0; r < KT; ++r) {
-                const T xs = __shfl_sync(SPT_FULL_MASK, t[r], s2);
-                // a select, not a zero coefficient: an overflowed x_s must
-                // not turn independent rows into NaN
-                t[r] = hit ? t[r] - cfr * xs : t[r];
-            }
-        }
-        // ---- publish: ring values, then the prefix (CTA-scope release),
-        // then the global copy (its readers are kc >= nwarps+2 groups later
-        // and synchronise through later releases)
+        sweep_scalar<T, KT>(t, dmask, coef, lane);
+        // ---- publish: ring values, then (release) the completed-group
+        // counter or, two-phase, the barrier arrival, then the global copy
         if (valid) store_vec<T, KT>(const_cast<T *>(sm.xr) + (pos & rmask) * KT, t);
         const bool hold = __any_sync(SPT_FULL_MASK, valid && i == withhold);
         __syncwarp();
-        if (lane == 0 && !hold) st_release_cta_smem(prefix, c + 1);
+        if (lane == 0 && !hold) {
+            if constexpr (TWO)
+                mbar_arrive(sm.bar + (c & (kc - 1)));
+            else
+                st_release_cta_smem(sm.ctr + 1, c + 1);
+        }
         if (valid) {
             T *xx = R.x + (int64_t)i * R.ld;
 #pragma unroll
             for (int r = 0; r < KT; ++r)
                 if (r < kt) xx[r] = t[r];
         }
+        __syncwarp();  // the coefficient table is rewritten by the next group
     }
+    return true;
 }
 
 // Entry used by the kernels: `nwarps` warps of the block work on the system
-// (the others return at once); one lane per row uses the column sweep.
-template <class T, int KT, bool TR>
+// (the others return at once); one lane per row uses the column sweep,
+// two-phase (TWO) or single-phase.
+template <class T, int KT, bool TR, bool TWO>
 __device__ __forceinline__ bool block_solve_any(const Sys<T> &A, const Rhs<T> &R, int rpw, int kc,
                                                 int P, int nwarps, const BlockSmem<T, KT> &sm,
                                                 const Waiter &w, int withhold)
 {
+    if (rpw == 32) {
+        // the sweep's global reads need kc >= 2 nwarps + 1 (always true for
+        // the plans' geometries; enforced here)
+        const int nw = max(1, min(nwarps, (kc - 1) / 2));
+        if ((int)(threadIdx.x >> 5) >= nw) return true;
+        return block_solve_sweep<T, KT, TR, TWO>(A, R, kc, P, nw, sm, w, withhold);
+    }
     if ((int)(threadIdx.x >> 5) >= nwarps) return true;
-    if (rpw == 32) return block_solve_sweep<T, KT, TR>(A, R, kc, P, nwarps, sm, w, withhold);
     return block_solve<T, KT, TR>(A, R, rpw, kc, P, sm, w, withhold);
 }
 
@@ -439,7 +491,8 @@ __device__ __forceinline__ BlockSmem<T, KT> carve_block_smem(unsigned char *raw,
                                                            int nw)
 {
     BlockSmem<T, KT> sm;
-    T *xr = reinterpret_cast<T *>(raw);
+    sm.bar = reinterpret_cast<uint64_t *>(raw);  // kc * 8 bytes keep what follows 16-byte aligned
+    T *xr = reinterpret_cast<T *>(raw + (size_t)kc * 8);
     sm.xr = xr;
     sm.coef = xr + (size_t)ring * KT;
     sm.xbuf = sm.coef + (size_t)nw * 1024;
@@ -450,13 +503,26 @@ __device__ __forceinline__ BlockSmem<T, KT> carve_block_smem(unsigned char *raw,
     return sm;
 }
 
+// Fresh state for one system (the barriers must not hold a live mbarrier:
+// first use of the memory, or release_block_smem ran).
 template <class T, int KT>
 __device__ __forceinline__ void reset_block_smem(const BlockSmem<T, KT> &sm, int ring, int kc)
 {
     for (int t = threadIdx.x; t < ring * KT; t += blockDim.x) sm.xr[t] = T(0);
     for (int t = threadIdx.x; t < ring; t += blockDim.x) sm.tag[t] = -1;
-    for (int t = threadIdx.x; t < kc; t += blockDim.x) sm.cdone[t] = -1;
+    for (int t = threadIdx.x; t < kc; t += blockDim.x) {
+        sm.cdone[t] = -1;
+        mbar_init(sm.bar + t, 1);
+    }
     if (threadIdx.x == 0) { sm.ctr[0] = 0; sm.ctr[1] = 0; }
+}
+
+// After a __syncthreads that ends the work on one system: invalidate the
+// barriers so that the memory can be re-initialised for the next one.
+template <class T, int KT>
+__device__ __forceinline__ void release_block_smem(const BlockSmem<T, KT> &sm, int kc)
+{
+    for (int t = threadIdx.x; t < kc; t += blockDim.x) mbar_inval(sm.bar + t);
 }
 
 }  // namespace spt

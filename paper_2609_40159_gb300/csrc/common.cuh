@@ -66,6 +66,43 @@ __device__ __forceinline__ void st_release_cta_smem(int *p, int v)
     asm volatile("st.release.cta.shared.s32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
 }
 
+// ------------------------------------------------------- shared mbarriers
+// Phase-completion barriers in shared memory.  A waiter blocked in
+// try_wait is suspended by the hardware until the phase completes (or a
+// hardware time limit passes), so waiting warps do not take issue slots from
+// the warps doing the work.
+__device__ __forceinline__ unsigned smem_addr(const void *p)
+{
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_inval(uint64_t *bar)
+{
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+// Arrive with release semantics at CTA scope (orders this thread's earlier
+// writes, and those ordered before it by __syncwarp, before the completion).
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.release.cta.shared::cta.b64 st, [%0];\n\t}" ::"r"(
+                     smem_addr(bar))
+                 : "memory");
+}
+// True once the phase of the given parity has completed (acquire, CTA scope).
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(ok)
+                 : "r"(smem_addr(bar)), "r"(parity)
+                 : "memory");
+    return ok != 0;
+}
+
 // Read-only (for the whole kernel) matrix data: non-coherent path.
 template <class T> __device__ __forceinline__ T ldro(const T *p) { return __ldg(p); }
 
@@ -117,6 +154,33 @@ struct WaitClock {
         return false;
     }
 };
+
+// Bound for waits whose every poll may block in hardware (mbarrier
+// try_wait): the clock is read at every poll, the abort flag every 64.
+struct WaitClockEach {
+    long long start = 0;
+    unsigned polls = 0;
+    __device__ __forceinline__ bool expired(const Waiter &w)
+    {
+        const long long t = clock64();
+        if (start == 0) { start = t; return false; }
+        if ((++polls & 63u) == 0 && aborted(w)) return true;
+        if ((double)(t - start) > 2.2 * (double)w.limit_ns) { give_up(w); return true; }
+        return false;
+    }
+};
+
+// Wait for phase `parity` of a shared mbarrier, bounded.  Every lane of the
+// warp calls it (no divergence around the wait); false on timeout / abort.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity, const Waiter &w)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    WaitClockEach clk;
+    for (;;) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (clk.expired(w)) return false;
+    }
+}
 
 // Global-memory polls back off exponentially (__nanosleep, 32 ns .. 512 ns)
 // so that thousands of waiting warps do not saturate the L2 slice that holds

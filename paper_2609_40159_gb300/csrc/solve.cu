@@ -380,14 +380,14 @@ k_block(Sys<T> A, Rhs<T> R, int rpw, int kc, int P, int nwarps, SyncArgs sy)
     BlockSmem<T, KT> sm = carve_block_smem<T, KT>(smraw, ring, kc, nwarps);
     reset_block_smem<T, KT>(sm, ring, kc);
     __syncthreads();
-    block_solve_any<T, KT, TR>(A, R, rpw, kc, P, nwarps, sm, sy.w, sy.withhold);
+    block_solve_any<T, KT, TR, true>(A, R, rpw, kc, P, nwarps, sm, sy.w, sy.withhold);
 }
 
 size_t block_smem_bytes(int rpw, int kt, int kc, bool f64, int nw)
 {
     const size_t ring = (size_t)kc * rpw;
     const size_t w = f64 ? 8 : 4;
-    return ring * kt * w + (size_t)nw * (1024 + 32) * w + ring * 4 + (size_t)kc * 4 + 16;
+    return (size_t)kc * 8 + ring * kt * w + (size_t)nw * (1024 + 32) * w + ring * 4 + (size_t)kc * 4 + 16;
 }
 // ------------------------------------------------------------- gradient
 template <class T>
@@ -571,7 +571,7 @@ cudaError_t solve_syncfree(const Sys<T> &A, const Rhs<T> &R, int rpw, int kt, bo
 }
 
 
-void block_geometry(int rpw, int kt, bool f64, int nwarps, int *kc, int *P)
+void block_geometry(int rpw, int kt, bool f64, int nwarps, int *kc, int *P, size_t grow_limit)
 {
     // Throttle distance P (row groups a group may run ahead of the completed
     // prefix) is about the number of active warps; the ring holds kc >= 2P
@@ -582,7 +582,7 @@ void block_geometry(int rpw, int kt, bool f64, int nwarps, int *kc, int *P)
     while (k < 2 * (nwarps + 2)) k <<= 1;
     while (k > 4 && block_smem_bytes(rpw, kt, k, f64, nwarps) > kBlockSmemBudget) k >>= 1;
     *P = k / 2;
-    while (k < 4096 / rpw && block_smem_bytes(rpw, kt, k * 2, f64, nwarps) <= kBlockSmemBudget / 2)
+    while (k < 4096 / rpw && block_smem_bytes(rpw, kt, k * 2, f64, nwarps) <= grow_limit)
         k <<= 1;  // a longer ring keeps more dependencies in shared memory
     *kc = k;
 }
@@ -616,7 +616,7 @@ static cudaError_t blk_launch(const Sys<T> &A, const Rhs<T> &R, int rpw, bool tr
                               const SyncArgs &sy, int nwarps, cudaStream_t s)
 {
     int kc, P;
-    block_geometry(rpw, KT, sizeof(T) == 8, nwarps, &kc, &P);
+    block_geometry(rpw, KT, sizeof(T) == 8, nwarps, &kc, &P, kBlockSmemBudget / 2);
     const size_t smem = block_smem_bytes(rpw, KT, kc, sizeof(T) == 8, nwarps);
     if (smem > kBlockSmemBudget) return cudaErrorInvalidConfiguration;
     const int tiles = (R.k + KT - 1) / KT;
@@ -644,7 +644,7 @@ bool block_mode_supported(int k, bool f64)
     if (k < 1) return false;
     const int kt = block_kt_for(k);
     int kc, P;
-    block_geometry(32, kt, f64, kMaxBlockWarps, &kc, &P);
+    block_geometry(32, kt, f64, kMaxBlockWarps, &kc, &P, kBlockSmemBudget / 2);
     return block_smem_bytes(32, kt, kc, f64, kMaxBlockWarps) <= kBlockSmemBudget;
 }
 

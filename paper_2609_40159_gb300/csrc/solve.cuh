@@ -98,12 +98,22 @@ bool block_mode_supported(int k, bool f64);
 int block_kt_for(int k);
 // Ring geometry of the block mode for `nwarps` active warps: kc row groups in
 // the ring, throttle distance P.
-void block_geometry(int rpw, int kt, bool f64, int nwarps, int *kc, int *P);
+// Ring length kc (row groups, a power of two >= 2 (nwarps + 2)) and
+// throttle distance P of the block algorithm; the ring grows while the
+// block's shared memory stays within grow_limit bytes.
+void block_geometry(int rpw, int kt, bool f64, int nwarps, int *kc, int *P, size_t grow_limit);
 // Active warps of the block mode for a system with the given level width.
 int block_warps_for(double rows_per_level, int rpw);
 size_t block_smem_bytes(int rpw, int kt, int kc, bool f64, int nw);
 // Most warps of a block-mode thread block that work on one system.
 constexpr int kMaxBlockWarps = 8;
+// Batched solve: warps per thread block and the minimum number of resident
+// blocks per SM the kernel is compiled for (0 = no register constraint).
+constexpr int kBatchWarps = 4;
+constexpr int kBatchMinBlocks = 0;
+// Shared memory a batched work item may grow its ring to: several items per
+// SM (each a latency-bound chain) beat longer rings.
+constexpr size_t kBatchSmemGrow = 48 * 1024;
 constexpr size_t kBlockSmemBudget = 200 * 1024;
 
 // ---------------------------------------------------------------- batched
@@ -145,15 +155,21 @@ cudaError_t batch_solve(const BatchMat *mats, const BatchItem *items, int32_t ni
                         const int32_t *order, const T *b, T *x, bool trans, PlanCtl *ctl,
                         const Waiter &w, int grid, size_t smem, long long *trace,
                         cudaStream_t s);
-// Value gradients of all matrices (row_off: nmat+1 prefix of n, device).
+// 32 consecutive rows (fewer at a system's end) of one system of a batch.
+struct RowChunk {
+    int32_t mat;
+    int32_t r0;  // a multiple of 32
+};
+// Value gradients of all matrices; chunks covers every row of every system
+// (device table of nchunks entries).
 template <class T>
-cudaError_t batch_grad_vals(const BatchMat *mats, int32_t nmat, const int64_t *row_off,
-                            int64_t total_rows, const T *gb, const T *x, T *gv, cudaStream_t s);
-// gb = gbp + T^T gbp for every rewritten matrix (packed buffers).
+cudaError_t batch_grad_vals(const BatchMat *mats, const RowChunk *chunks, int64_t nchunks, const T *gb,
+                            const T *x, T *gv, cudaStream_t s);
+// gb = gbp + T^T gbp for every rewritten matrix (packed buffers); tchunks
+// lists the chunks that hold at least one row of T.
 template <class T>
-cudaError_t batch_tt_apply(const BatchMat *mats, int32_t nmat, const int64_t *row_off,
-                           int64_t total_rows, int64_t total_rhs, const T *gbp, T *gb,
-                           cudaStream_t s);
+cudaError_t batch_tt_apply(const BatchMat *mats, const RowChunk *tchunks, int64_t ntchunks,
+                           int64_t total_rhs, const T *gbp, T *gb, cudaStream_t s);
 int batch_grid(size_t smem, const DeviceInfo &di);
 
 }  // namespace spt
