@@ -44,7 +44,7 @@ FALLBACK_HBM = 6800.0
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--nmat", type=int, default=512)
@@ -412,13 +412,14 @@ def main():
             "solves_per_s": world * len(items) / (ms_step * 1e-3),
             "phase_ms": {"fwd": f_ms, "transpose": t_ms, "tt_and_grad": r_ms},
             "fwd_only_gbs": bf / (f_ms * 1e-3) / 1e9,
+            "algorithmic_bytes": {"fwd_solve": bf, "transpose_solve": b_solveT, "step": step_bytes},
             "levels": {"max_orig": int(nlev[:, 0].max()), "max_rewritten": int(nlev[1::2, 1].max()),
                        "sum_orig": int(nlev[:, 0].sum()), "sum_after": int(nlev[:, 1].sum())},
             "preprocess_s": {"analyze": t_an, "rewrite": t_rw, "plan": t_plan, "total": t_prep},
             "autotune": None if tune is None else {"choice": tune["choice"], "ms": tune["ms"]},
             "roofline": roofline,
             "clocks": clocks,
-            "gpu_launches": 6 * K,
+            "gpu_launches": 7 * K,
             "e2e": e2e,
         }
         line.update(extras)

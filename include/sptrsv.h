@@ -183,7 +183,9 @@ sptrsv_status sptrsv_plan_set(sptrsv_plan plan, int32_t mode, int32_t rows_per_w
 sptrsv_status sptrsv_solve(sptrsv_plan plan, const void *b, void *x, int32_t nrhs, int64_t ld);
 
 /* Adjoint of the solve: g_b = L^{-T} g_x, processed in reverse level /
- * reverse row order.  Requires build_transpose.  Asynchronous.              */
+ * reverse row order.  Requires build_transpose.  Asynchronous.  First
+ * gathers L's current values into CSC order (one elementwise launch, plan-
+ * owned buffer), so values may change between calls.                      */
 sptrsv_status sptrsv_solve_transpose(sptrsv_plan plan, const void *gx, void *gb, int32_t nrhs,
                                      int64_t ld);
 
@@ -219,7 +221,8 @@ sptrsv_status sptrsv_batch_offsets(sptrsv_plan plan, int64_t *rhs_offset, int64_
  * geometry).  Synchronises.                                               */
 sptrsv_status sptrsv_batch_plan_set(sptrsv_plan plan, const int32_t *rows_per_warp,
                                     const int32_t *rhs_tile);
-/* All systems in one persistent launch (plus a tiny reset launch): no host
+/* All systems in one persistent launch (plus a tiny reset launch; the
+ * transpose solve also gathers the values into CSC order first): no host
  * work per matrix, so the call can be captured in a CUDA graph.            */
 sptrsv_status sptrsv_batch_solve(sptrsv_plan plan, const void *b, void *x);
 sptrsv_status sptrsv_batch_solve_transpose(sptrsv_plan plan, const void *gx, void *gb);

@@ -82,6 +82,7 @@ struct PlanMat {
     int32_t *d_lev = nullptr, *d_perm = nullptr, *d_level_ptr = nullptr;
     std::vector<int32_t> h_level_ptr;
     int32_t *d_cp = nullptr, *d_crow = nullptr, *d_tmap = nullptr;
+    void *d_cv = nullptr;  // L's values in CSC order (transpose solves)
     uint32_t *d_tmask = nullptr;
 };
 
@@ -273,7 +274,7 @@ template <class T> Sys<T> sys_of(const PlanMat &M)
     Sys<T> A;
     A.n = M.L.n;
     A.rp = M.L.row_ptr; A.ci = M.L.col_idx; A.v = (const T *)M.L.vals;
-    A.cp = M.d_cp; A.crow = M.d_crow; A.tmap = M.d_tmap;
+    A.cp = M.d_cp; A.crow = M.d_crow; A.tmap = M.d_tmap; A.cv = (const T *)M.d_cv;
     A.trp = M.hasT ? M.T.row_ptr : nullptr;
     A.tci = M.hasT ? M.T.col_idx : nullptr;
     A.tv = M.hasT ? (const T *)M.T.vals : nullptr;
@@ -319,6 +320,8 @@ sptrsv_status prepare_mat(sptrsv_plan p, PlanMat &M, const sptrsv_csr &L, const 
         e = p->alloc(&M.d_cp, sizeof(int32_t) * (nn + 1));
         if (e == cudaSuccess) e = p->alloc(&M.d_crow, sizeof(int32_t) * (size_t)(L.nnz > 0 ? L.nnz : 1));
         if (e == cudaSuccess) e = p->alloc(&M.d_tmap, sizeof(int32_t) * (size_t)(L.nnz > 0 ? L.nnz : 1));
+        if (e == cudaSuccess)
+            e = p->alloc(&M.d_cv, (L.dtype == SPTRSV_F64 ? 8 : 4) * (size_t)(L.nnz > 0 ? L.nnz : 1));
         if (e == cudaSuccess) e = build_csc(L.row_ptr, L.col_idx, n, L.nnz, M.d_cp, M.d_crow, M.d_tmap, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return from_cuda(e);
@@ -367,6 +370,10 @@ sptrsv_status solve_impl(sptrsv_plan p, const void *b, void *x, int32_t nrhs, in
     cudaStream_t s = p->h->stream;
     Sys<T> A = sys_of<T>(M);
     Rhs<T> R{(const T *)b, (T *)x, ld, nrhs};
+    if (trans) {
+        cudaError_t eg = csc_values<T>(M.d_tmap, (const T *)M.L.vals, (T *)M.d_cv, M.L.nnz, s);
+        if (eg != cudaSuccess) return from_cuda(eg);
+    }
     SyncArgs sy{p->d_flags, p->d_ctl, p->withhold, Waiter{p->h->d_status, &p->d_ctl->abort_flag, p->spin}};
     const int kt = std::min(p->kt, default_kt(nrhs));
     cudaError_t e = cudaSuccess;
@@ -680,7 +687,7 @@ extern "C" sptrsv_status sptrsv_batch_plan_create(sptrsv_handle h, int32_t nmat,
         B.k = nrhs[m];
         B.nnz = M.L.nnz;
         B.rp = M.L.row_ptr; B.ci = M.L.col_idx; B.v = M.L.vals;
-        B.cp = M.d_cp; B.crow = M.d_crow; B.tmap = M.d_tmap;
+        B.cp = M.d_cp; B.crow = M.d_crow; B.tmap = M.d_tmap; B.cv = M.d_cv;
         B.trp = M.hasT ? M.T.row_ptr : nullptr;
         B.tci = M.hasT ? M.T.col_idx : nullptr;
         B.tv = M.hasT ? M.T.vals : nullptr;
@@ -775,7 +782,11 @@ sptrsv_status batch_solve_impl(sptrsv_plan p, const void *b, void *x, bool trans
     if (!b || !x) return SPTRSV_EINVAL;
     if (trans && !p->have_csc) return SPTRSV_ENOTSUP;
     Waiter w{p->h->d_status, &p->d_ctl->abort_flag, p->spin};
-    cudaError_t e;
+    cudaError_t e = cudaSuccess;
+    if (trans)
+        e = p->dtype == SPTRSV_F64 ? batch_csc_values<double>(p->d_mats, (int32_t)p->mats.size(), p->h->stream)
+                                   : batch_csc_values<float>(p->d_mats, (int32_t)p->mats.size(), p->h->stream);
+    if (e != cudaSuccess) return from_cuda(e);
     if (p->dtype == SPTRSV_F64)
         e = batch_solve<double>(p->d_mats, p->d_items, p->nitems, p->d_order, (const double *)b, (double *)x,
                                 trans, p->d_ctl, w, p->batch_grid_sz, p->batch_smem, p->d_trace, p->h->stream);

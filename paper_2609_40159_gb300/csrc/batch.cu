@@ -19,7 +19,7 @@ __device__ __forceinline__ Sys<T> sys_of(const BatchMat &M)
     Sys<T> A;
     A.n = M.n;
     A.rp = M.rp; A.ci = M.ci; A.v = (const T *)M.v;
-    A.cp = M.cp; A.crow = M.crow; A.tmap = M.tmap;
+    A.cp = M.cp; A.crow = M.crow; A.tmap = M.tmap; A.cv = (const T *)M.cv;
     A.trp = M.trp; A.tci = M.tci; A.tv = (const T *)M.tv; A.tmask = M.tmask;
     return A;
 }
@@ -102,39 +102,52 @@ __device__ __forceinline__ int row_in_chunk(int s, int nrows, int p)
 }
 
 // dL/dL_ij = -g_b[i,:] . x[j,:] on L's pattern.  One warp per 32-row chunk;
-// the chunk's nonzeros are contiguous in CSR order and are taken 32 at a
-// time, one per lane (coalesced column indices and gradient stores).
+// the chunk's nonzeros are contiguous in CSR order.  G lanes share a
+// nonzero (lane s of the group takes the columns s, s + G, ..., and the
+// partial sums are added with shuffles); the warp takes 32 / G nonzeros at
+// a time (coalesced column indices and gradient stores).  G = 1 measured
+// best on the batched workload: wider groups multiply the per-window row
+// search and reduction.
+template <class T, int G>
+__device__ __forceinline__ void grad_chunk(const BatchMat &M, int r0, const T *gb, const T *x, T *gv)
+{
+    const int lane = threadIdx.x & 31;
+    const int nrows = min(32, M.n - r0);
+    const int k = M.k;
+    const int s = ldro(M.rp + r0 + min(lane, nrows));
+    const int pe = __shfl_sync(SPT_FULL_MASK, s, nrows & 31);
+    const int end = nrows == 32 ? ldro(M.rp + r0 + 32) : pe;
+    const int p0 = __shfl_sync(SPT_FULL_MASK, s, 0);
+    const T *xb = x + M.rhs_off;
+    const T *gbb = gb + M.rhs_off;
+    T *out = gv + M.vals_off;
+    const int g = lane / G, sl = lane % G;
+    for (int base = p0; base < end; base += 32 / G) {
+        const int p = base + g;
+        const int r = row_in_chunk(s, nrows, p);
+        T acc = T(0);
+        if (p < end) {
+            const T *gi = gbb + (int64_t)(r0 + r) * k;
+            const T *xj = xb + (int64_t)ldro(M.ci + p) * k;
+            for (int q = sl; q < k; q += G) acc += gi[q] * xj[q];
+        }
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(SPT_FULL_MASK, acc, o);
+        if (p < end && sl == 0) out[p] = -acc;
+    }
+}
+
 template <class T>
 __global__ void k_batch_grad(const BatchMat *__restrict__ mats, const RowChunk *__restrict__ chunks,
                              int64_t nchunks, const T *__restrict__ gb, const T *__restrict__ x,
                              T *__restrict__ gv)
 {
-    const int lane = threadIdx.x & 31;
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t c = gw; c < nchunks; c += nw) {
         const RowChunk ch = chunks[c];
         const BatchMat &M = mats[ch.mat];
-        const int nrows = min(32, M.n - ch.r0);
-        const int k = M.k;
-        const int s = ldro(M.rp + ch.r0 + min(lane, nrows));
-        const int pe = __shfl_sync(SPT_FULL_MASK, s, nrows & 31);
-        const int end = nrows == 32 ? ldro(M.rp + ch.r0 + 32) : pe;
-        const int p0 = __shfl_sync(SPT_FULL_MASK, s, 0);
-        const T *xb = x + M.rhs_off;
-        const T *gbb = gb + M.rhs_off;
-        T *out = gv + M.vals_off;
-        for (int base = p0; base < end; base += 32) {
-            const int p = base + lane;
-            const int r = row_in_chunk(s, nrows, p);
-            if (p < end) {
-                const T *gi = gbb + (int64_t)(ch.r0 + r) * k;
-                const T *xj = xb + (int64_t)ldro(M.ci + p) * k;
-                T acc = T(0);
-                for (int q = 0; q < k; ++q) acc += gi[q] * xj[q];
-                out[p] = -acc;
-            }
-        }
+        grad_chunk<T, 1>(M, ch.r0, gb, x, gv);
     }
 }
 
@@ -163,6 +176,21 @@ __global__ void k_batch_tt(const BatchMat *__restrict__ mats, const RowChunk *__
                 for (int q = 0; q < k; ++q) atomicAdd(gj + q, cv * gi[q]);
             }
         }
+    }
+}
+
+// cv = v[tmap] for every system: blockIdx.y picks the system.
+template <class T>
+__global__ void k_batch_csc_values(const BatchMat *__restrict__ mats, int32_t nmat)
+{
+    for (int m = blockIdx.y; m < nmat; m += gridDim.y) {
+        const BatchMat &M = mats[m];
+        if (M.cv == nullptr) continue;
+        const T *v = (const T *)M.v;
+        T *cv = (T *)M.cv;
+        for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < M.nnz;
+             q += (int64_t)gridDim.x * blockDim.x)
+            cv[q] = ldro(v + ldro(M.tmap + q));
     }
 }
 
@@ -224,6 +252,15 @@ cudaError_t batch_tt_apply(const BatchMat *mats, const RowChunk *tchunks, int64_
     return cudaGetLastError();
 }
 
+template <class T>
+cudaError_t batch_csc_values(const BatchMat *mats, int32_t nmat, cudaStream_t s)
+{
+    if (nmat <= 0) return cudaSuccess;
+    const dim3 grid(64, (unsigned)std::min(nmat, 65535));
+    k_batch_csc_values<T><<<grid, 256, 0, s>>>(mats, nmat);
+    return cudaGetLastError();
+}
+
 #define SPT_INST(T)                                                                              \
     template cudaError_t batch_solve<T>(const BatchMat *, const BatchItem *, int32_t,             \
                                         const int32_t *, const T *, T *, bool, PlanCtl *,        \
@@ -231,7 +268,8 @@ cudaError_t batch_tt_apply(const BatchMat *mats, const RowChunk *tchunks, int64_
     template cudaError_t batch_grad_vals<T>(const BatchMat *, const RowChunk *, int64_t,         \
                                             const T *, const T *, T *, cudaStream_t);            \
     template cudaError_t batch_tt_apply<T>(const BatchMat *, const RowChunk *, int64_t, int64_t, \
-                                           const T *, T *, cudaStream_t);
+                                           const T *, T *, cudaStream_t);                        \
+    template cudaError_t batch_csc_values<T>(const BatchMat *, int32_t, cudaStream_t);
 SPT_INST(double)
 SPT_INST(float)
 #undef SPT_INST

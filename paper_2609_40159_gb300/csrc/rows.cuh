@@ -1,5 +1,6 @@
 // Row views of a system for the solve kernels: the forward solve reads L by
-// rows (CSR), the transpose solve reads L by columns (CSC + value map).
+// rows (CSR), the transpose solve reads L by columns (CSC, values gathered
+// into CSC order before the solve).
 #pragma once
 
 #include "solve.cuh"
@@ -20,9 +21,9 @@ template <class T> struct RV<T, false> {
 template <class T> struct RV<T, true> {
     static __device__ __forceinline__ int beg(const Sys<T> &A, int i) { return ldro(A.cp + i) + 1; }
     static __device__ __forceinline__ int end(const Sys<T> &A, int i) { return ldro(A.cp + i + 1); }
-    static __device__ __forceinline__ T diag(const Sys<T> &A, int b, int) { return ldro(A.v + ldro(A.tmap + b - 1)); }
+    static __device__ __forceinline__ T diag(const Sys<T> &A, int b, int) { return ldro(A.cv + b - 1); }
     static __device__ __forceinline__ int col(const Sys<T> &A, int q) { return ldro(A.crow + q); }
-    static __device__ __forceinline__ T val(const Sys<T> &A, int q) { return ldro(A.v + ldro(A.tmap + q)); }
+    static __device__ __forceinline__ T val(const Sys<T> &A, int q) { return ldro(A.cv + q); }
 };
 
 template <class T>
@@ -57,7 +58,7 @@ __device__ __forceinline__ void prefetch_row(const Sys<T> &A, int i)
     } else {
         const int a = ldro(A.cp + i);
         prefetch_l2(A.crow + a);
-        prefetch_l2(A.tmap + a);
+        prefetch_l2(A.cv + a);
     }
 }
 

@@ -683,6 +683,25 @@ int persistent_grid_syncfree(int kt, bool f64, const DeviceInfo &di)
     return per_sm * di.num_sms;
 }
 
+// ------------------------------------------------------ CSC values
+template <class T>
+__global__ void k_csc_values(const int32_t *__restrict__ tmap, const T *__restrict__ v, T *__restrict__ cv,
+                             int64_t nnz)
+{
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nnz;
+         q += (int64_t)gridDim.x * blockDim.x)
+        cv[q] = ldro(v + ldro(tmap + q));
+}
+
+template <class T>
+cudaError_t csc_values(const int32_t *tmap, const T *v, T *cv, int64_t nnz, cudaStream_t s)
+{
+    if (nnz <= 0) return cudaSuccess;
+    const int64_t blocks = std::min<int64_t>((nnz + 255) / 256, 152 * 16);
+    k_csc_values<T><<<(int)blocks, 256, 0, s>>>(tmap, v, cv, nnz);
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------ explicit instantiations
 #define SPT_INST(T)                                                                                     \
     template cudaError_t launch_prologue<T>(PlanCtl *, cudaStream_t);                                   \
@@ -697,7 +716,8 @@ int persistent_grid_syncfree(int kt, bool f64, const DeviceInfo &di)
                                         const SyncArgs &, int, cudaStream_t);                           \
     template cudaError_t grad_vals<T>(const Sys<T> &, const T *, const T *, int64_t, int32_t, T *,      \
                                       cudaStream_t);                                                    \
-    template cudaError_t tt_apply<T>(const Sys<T> &, const T *, T *, int64_t, int32_t, cudaStream_t);
+    template cudaError_t tt_apply<T>(const Sys<T> &, const T *, T *, int64_t, int32_t, cudaStream_t);   \
+    template cudaError_t csc_values<T>(const int32_t *, const T *, T *, int64_t, cudaStream_t);
 SPT_INST(double)
 SPT_INST(float)
 #undef SPT_INST

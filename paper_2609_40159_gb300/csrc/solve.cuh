@@ -15,7 +15,9 @@ template <class T> struct Sys {
     const T *v;
     const int32_t *cp;    // CSC of L (transpose solve): column pointers,
     const int32_t *crow;  //   row of every CSC entry (diagonal first),
-    const int32_t *tmap;  //   CSR position of every CSC entry
+    const int32_t *tmap;  //   CSR position of every CSC entry,
+    const T *cv;          //   value of every CSC entry (v[tmap[q]], gathered
+                          //   before each transpose solve)
     const int32_t *trp;   // T of a rewritten system (rows with entries only)
     const int32_t *tci;
     const T *tv;
@@ -125,6 +127,7 @@ struct BatchMat {
     const int32_t *rp, *ci;
     const void *v;
     const int32_t *cp, *crow, *tmap;
+    void *cv;  // CSC values, gathered before each transpose solve
     const int32_t *trp, *tci;
     const void *tv;
     const uint32_t *tmask;
@@ -155,6 +158,14 @@ cudaError_t batch_solve(const BatchMat *mats, const BatchItem *items, int32_t ni
                         const int32_t *order, const T *b, T *x, bool trans, PlanCtl *ctl,
                         const Waiter &w, int grid, size_t smem, long long *trace,
                         cudaStream_t s);
+// cv[q] = v[tmap[q]]: the values of L in CSC order, so that the transpose
+// solves read them without the indirection (refreshed before every
+// transpose solve: the plan does not assume that L's values stay fixed).
+template <class T>
+cudaError_t csc_values(const int32_t *tmap, const T *v, T *cv, int64_t nnz, cudaStream_t s);
+template <class T>
+cudaError_t batch_csc_values(const BatchMat *mats, int32_t nmat, cudaStream_t s);
+
 // 32 consecutive rows (fewer at a system's end) of one system of a batch.
 struct RowChunk {
     int32_t mat;
