@@ -390,6 +390,11 @@ def main():
                "h2d_bytes_per_step": int(hb.numel() * 4 + hw.numel() * 4),
                "d2h_bytes_per_step": int(hx.numel() * 4 + hgb.numel() * 4 + hgv.numel() * 4)}
 
+    # one host-side gather of every rank's report (no collective in the data path)
+    from paper_2609_40159_gb300 import shard
+    reports = shard.gather_reports({"rank": rank, "systems": len(items), "status": int(status),
+                                    "ms_per_step": tot_ms / K, "phase_ms": [f_ms, t_ms, r_ms]}, dist)
+
     extras = {}
     if rank == 0 and not args.no_extras and not args.ncu:
         extras = run_extras(P, items, mats, dev, bf)
@@ -422,6 +427,8 @@ def main():
             "gpu_launches": 7 * K,
             "e2e": e2e,
         }
+        if world > 1:
+            line["per_rank"] = reports
         line.update(extras)
         print(json.dumps(line), flush=True)
     if dist:

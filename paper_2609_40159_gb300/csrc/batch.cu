@@ -102,52 +102,41 @@ __device__ __forceinline__ int row_in_chunk(int s, int nrows, int p)
 }
 
 // dL/dL_ij = -g_b[i,:] . x[j,:] on L's pattern.  One warp per 32-row chunk;
-// the chunk's nonzeros are contiguous in CSR order.  G lanes share a
-// nonzero (lane s of the group takes the columns s, s + G, ..., and the
-// partial sums are added with shuffles); the warp takes 32 / G nonzeros at
-// a time (coalesced column indices and gradient stores).  G = 1 measured
-// best on the batched workload: wider groups multiply the per-window row
-// search and reduction.
-template <class T, int G>
-__device__ __forceinline__ void grad_chunk(const BatchMat &M, int r0, const T *gb, const T *x, T *gv)
-{
-    const int lane = threadIdx.x & 31;
-    const int nrows = min(32, M.n - r0);
-    const int k = M.k;
-    const int s = ldro(M.rp + r0 + min(lane, nrows));
-    const int pe = __shfl_sync(SPT_FULL_MASK, s, nrows & 31);
-    const int end = nrows == 32 ? ldro(M.rp + r0 + 32) : pe;
-    const int p0 = __shfl_sync(SPT_FULL_MASK, s, 0);
-    const T *xb = x + M.rhs_off;
-    const T *gbb = gb + M.rhs_off;
-    T *out = gv + M.vals_off;
-    const int g = lane / G, sl = lane % G;
-    for (int base = p0; base < end; base += 32 / G) {
-        const int p = base + g;
-        const int r = row_in_chunk(s, nrows, p);
-        T acc = T(0);
-        if (p < end) {
-            const T *gi = gbb + (int64_t)(r0 + r) * k;
-            const T *xj = xb + (int64_t)ldro(M.ci + p) * k;
-            for (int q = sl; q < k; q += G) acc += gi[q] * xj[q];
-        }
-#pragma unroll
-        for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(SPT_FULL_MASK, acc, o);
-        if (p < end && sl == 0) out[p] = -acc;
-    }
-}
-
+// the chunk's nonzeros are contiguous in CSR order and are taken 32 at a
+// time, one per lane (coalesced column indices and gradient stores).
+// (Groups of up to 8 lanes per nonzero, reading g_b[i,:] and x[j,:] in
+// contiguous pieces, measured slower on the batched workload.)
 template <class T>
 __global__ void k_batch_grad(const BatchMat *__restrict__ mats, const RowChunk *__restrict__ chunks,
                              int64_t nchunks, const T *__restrict__ gb, const T *__restrict__ x,
                              T *__restrict__ gv)
 {
+    const int lane = threadIdx.x & 31;
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t c = gw; c < nchunks; c += nw) {
         const RowChunk ch = chunks[c];
         const BatchMat &M = mats[ch.mat];
-        grad_chunk<T, 1>(M, ch.r0, gb, x, gv);
+        const int nrows = min(32, M.n - ch.r0);
+        const int k = M.k;
+        const int s = ldro(M.rp + ch.r0 + min(lane, nrows));
+        const int pe = __shfl_sync(SPT_FULL_MASK, s, nrows & 31);
+        const int end = nrows == 32 ? ldro(M.rp + ch.r0 + 32) : pe;
+        const int p0 = __shfl_sync(SPT_FULL_MASK, s, 0);
+        const T *xb = x + M.rhs_off;
+        const T *gbb = gb + M.rhs_off;
+        T *out = gv + M.vals_off;
+        for (int base = p0; base < end; base += 32) {
+            const int p = base + lane;
+            const int r = row_in_chunk(s, nrows, p);
+            if (p < end) {
+                const T *gi = gbb + (int64_t)(ch.r0 + r) * k;
+                const T *xj = xb + (int64_t)ldro(M.ci + p) * k;
+                T acc = T(0);
+                for (int q = 0; q < k; ++q) acc += gi[q] * xj[q];
+                out[p] = -acc;
+            }
+        }
     }
 }
 
