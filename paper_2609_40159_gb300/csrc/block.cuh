@@ -355,12 +355,20 @@ __device__ bool block_solve_sweep(const Sys<T> &A, const Rhs<T> &R, int kc, int 
             coef[(in ? jj[u] - base : 31) * 32 + lane] = vv[u] * rinv;
             dmask |= in ? (1u << (jj[u] - base)) : 0u;
         }
+        // entries beyond the first NP (long rows; in the transpose view,
+        // columns longer than NP -- there the farthest entries): in-group
+        // ones go to the table; the others are classified so that only the
+        // rare ones in group c-1 are left for the group's turn
         const bool longrow = valid && e - a > NP;
+        bool tail_near = false, tail_ring = false;
         for (int p = a + NP; longrow && p < e; ++p) {
             const int pj = order_pos<TR>(n, RV<T, TR>::col(A, p));
             if (pj >= base) {
                 dmask |= 1u << (pj - base);
                 coef[(pj - base) * 32 + lane] = RV<T, TR>::val(A, p) * rinv;
+            } else if (c - (pj >> 5) < kc) {
+                if (pj >= base - 32) tail_near = true;
+                else tail_ring = true;
             }
         }
         const bool anylong = __any_sync(SPT_FULL_MASK, longrow);
@@ -384,7 +392,7 @@ __device__ bool block_solve_sweep(const Sys<T> &A, const Rhs<T> &R, int kc, int 
                     }
                 }
             }
-            for (int p = a + NP; longrow && p < e; ++p) {
+            for (int p = a + NP; anylong && longrow && p < e; ++p) {
                 const int j = RV<T, TR>::col(A, p);
                 if (c - (order_pos<TR>(n, j) >> 5) >= kc) {
                     const T v = RV<T, TR>::val(A, p);
@@ -401,10 +409,24 @@ __device__ bool block_solve_sweep(const Sys<T> &A, const Rhs<T> &R, int kc, int 
         for (int r = 0; r < KT; ++r) consume(bv[r]);
         // ---- 2. groups <= c-2 (group g's arrival is phase g / kc of
         // barrier g % kc); single-phase: all earlier groups (the completed-
-        // group counter reaches c; every lane polls it)
+        // group counter reaches c; every lane polls it), after the ring
+        // entries of the row tails that are in groups <= c-2 (waited for
+        // separately, so that their divergent loop runs while group c-1 is
+        // being solved)
         if constexpr (TWO) {
             if (c >= 2) ok = mbar_wait(sm.bar + ((c - 2) & (kc - 1)), ((unsigned)(c - 2) / kc) & 1u, w);
         } else {
+            if (__any_sync(SPT_FULL_MASK, tail_ring)) {
+                WaitClock clk;
+                while (ld_acquire_cta_smem(sm.ctr + 1) < c - 1)
+                    if (clk.expired(w)) { ok = false; break; }
+                if (!__all_sync(SPT_FULL_MASK, ok)) return false;
+                for (int p = a + NP; tail_ring && p < e; ++p) {
+                    const int pj = order_pos<TR>(n, RV<T, TR>::col(A, p));
+                    if (pj < base - 32 && c - (pj >> 5) < kc)
+                        axpy_vec<T, KT>(RV<T, TR>::val(A, p), ring0 + (pj & rmask) * KT, acc);
+                }
+            }
             WaitClock clk;
             while (ld_acquire_cta_smem(sm.ctr + 1) < c)
                 if (clk.expired(w)) { ok = false; break; }
@@ -416,10 +438,18 @@ __device__ bool block_solve_sweep(const Sys<T> &A, const Rhs<T> &R, int kc, int 
             const bool use = valid && a + u < e && jj[u] < lim && c - (jj[u] >> 5) < kc;
             axpy_vec<T, KT>(use ? vv[u] : T(0), ring0 + (use ? (jj[u] & rmask) * KT : 0), acc);
         }
-        if (anylong) {
-            for (int p = a + NP; longrow && p < e; ++p) {
+        if constexpr (TWO) {
+            if (__any_sync(SPT_FULL_MASK, tail_ring)) {
+                for (int p = a + NP; tail_ring && p < e; ++p) {
+                    const int pj = order_pos<TR>(n, RV<T, TR>::col(A, p));
+                    if (pj < base - 32 && c - (pj >> 5) < kc)
+                        axpy_vec<T, KT>(RV<T, TR>::val(A, p), ring0 + (pj & rmask) * KT, acc);
+                }
+            }
+        } else if (__any_sync(SPT_FULL_MASK, tail_near)) {
+            for (int p = a + NP; tail_near && p < e; ++p) {
                 const int pj = order_pos<TR>(n, RV<T, TR>::col(A, p));
-                if (pj < lim && c - (pj >> 5) < kc)
+                if (pj < base && pj >= base - 32)
                     axpy_vec<T, KT>(RV<T, TR>::val(A, p), ring0 + (pj & rmask) * KT, acc);
             }
         }
@@ -432,8 +462,8 @@ __device__ bool block_solve_sweep(const Sys<T> &A, const Rhs<T> &R, int kc, int 
                 const bool prev = valid && a + u < e && jj[u] < base && jj[u] >= base - 32;
                 axpy_vec<T, KT>(prev ? vv[u] : T(0), ring0 + (prev ? (jj[u] & rmask) * KT : 0), acc);
             }
-            if (anylong) {
-                for (int p = a + NP; longrow && p < e; ++p) {
+            if (__any_sync(SPT_FULL_MASK, tail_near)) {
+                for (int p = a + NP; tail_near && p < e; ++p) {
                     const int pj = order_pos<TR>(n, RV<T, TR>::col(A, p));
                     if (pj < base && pj >= base - 32)
                         axpy_vec<T, KT>(RV<T, TR>::val(A, p), ring0 + (pj & rmask) * KT, acc);
