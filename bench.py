@@ -397,27 +397,27 @@ def main():
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(sh)
         for t in range(Ke):
-            S = sets[t % 2]
+            bs = sets[t % 2]
             with torch.cuda.stream(sh):
                 if comp_done[t % 2] is not None:
                     sh.wait_event(comp_done[t % 2])  # step t-2 no longer reads this set
-                S["b"].copy_(hb, non_blocking=True)
-                S["w"].copy_(hw, non_blocking=True)
+                bs["b"].copy_(hb, non_blocking=True)
+                bs["w"].copy_(hw, non_blocking=True)
                 h2d = ev()
                 h2d.record(sh)
             with torch.cuda.stream(s):
                 s.wait_event(h2d)
                 if d2h_done[t % 2] is not None:
                     s.wait_event(d2h_done[t % 2])  # step t-2's results are copied out
-                for g in S["graphs"]:
+                for g in bs["graphs"]:
                     g.replay()
                 comp_done[t % 2] = ev()
                 comp_done[t % 2].record(s)
             with torch.cuda.stream(sd):
                 sd.wait_event(comp_done[t % 2])
-                hx.copy_(S["x"], non_blocking=True)
-                hgb.copy_(S["gb"], non_blocking=True)
-                hgv.copy_(S["gv"], non_blocking=True)
+                hx.copy_(bs["x"], non_blocking=True)
+                hgb.copy_(bs["gb"], non_blocking=True)
+                hgv.copy_(bs["gv"], non_blocking=True)
                 d2h_done[t % 2] = ev()
                 d2h_done[t % 2].record(sd)
         with torch.cuda.stream(sd):
