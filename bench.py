@@ -480,6 +480,77 @@ def main():
         dist.destroy_process_group()
 
 
+def _host_ms(fn, reps=3):
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    best = float("inf")
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        fn()
+        torch.cuda.synchronize()
+        best = min(best, 1e3 * (time.perf_counter() - t0))
+    return best
+
+
+def _single_config(P, A_h, dev, k, autotune):
+    """Analysis, rewrite (narrowest-level 1 %, chunks of 8 levels) and the
+    forward solve in every mode on the original and the rewritten DAG."""
+    import torch
+    A = P.Matrix.from_host(A_h, device=dev)
+    an = P.analyze(A)
+    rows, tg = S.narrowest_levels_list(an.nlevels, an.level_ptr.cpu().numpy(), an.perm.cpu().numpy(), 0.01, 8)
+    Lp, T = P.rewrite(A, an.lev, rows, tg)
+    an2 = P.analyze(Lp, prev_lev=an.lev, first_row=int(np.min(rows)))
+    res = {"n": A.n, "nnz": A.nnz, "levels_orig": an.nlevels, "levels_rewritten": an2.nlevels,
+           "cv_cost_orig": float(an.stats[3]), "cv_cost_rewritten": float(an2.stats[3]),
+           "rows_rewritten": int(len(rows)), "nnz_T": int(T.nnz), "nnz_Lp": int(Lp.nnz),
+           "preprocess_ms": {"analyze": _host_ms(lambda: P.analyze(A)),
+                             "rewrite_1pct": _host_ms(lambda: P.rewrite(A, an.lev, rows, tg)),
+                             "analyze_incremental_after_rewrite":
+                                 _host_ms(lambda: P.analyze(Lp, prev_lev=an.lev, first_row=int(np.min(rows))))}}
+    b = torch.as_tensor(S.rhs(A_h.n, k, seed=1)).to(dev)
+    x = torch.empty_like(b)
+    modes = {}
+    for name, (M, TT) in {"orig": (A, None), "rewritten": (Lp, T)}.items():
+        p = P.Plan(M, TT)
+        nb = bytes_fwd(M.n, M.nnz, k, 8, M.n if TT is not None else 0, TT.nnz if TT is not None else 0)
+        for mode in ("level_launch", "level", "syncfree"):
+            p.set(mode, 0, 0)
+            ms = autotune.time_call(lambda: p.solve(b, out=x), reps=3, warmup=1)
+            modes[f"{name}:{mode}"] = {"us": 1e3 * ms, "gbs": nb / (ms * 1e-3) / 1e9}
+    res["fwd"] = modes
+    return res
+
+
+def _diff_config(P, A_h, dev, k, autotune):
+    """Differentiated solve (autograd): forward + adjoint (transpose solve,
+    value gradient, T^T for the rewritten system), original and rewritten."""
+    import torch
+    A = P.Matrix.from_host(A_h, device=dev)
+    an = P.analyze(A)
+    rows, tg = S.narrowest_levels_list(an.nlevels, an.level_ptr.cpu().numpy(), an.perm.cpu().numpy(), 0.01, 8)
+    Lp, T = P.rewrite(A, an.lev, rows, tg)
+    b = torch.as_tensor(S.rhs(A_h.n, k, seed=4)).to(dev)
+    w = torch.as_tensor(S.rhs(A_h.n, k, seed=5)).to(dev)
+    res = {"n": A.n, "nnz": A.nnz, "k": k, "levels_orig": an.nlevels}
+    for name, (M, TT) in {"orig": (A, None), "rewritten": (Lp, T)}.items():
+        p = P.Plan(M, TT, transpose=True)
+        vals = M.vals.clone().requires_grad_(True)
+        bb = b.clone().requires_grad_(True)
+
+        def step():
+            xx = P.solve(p, bb, vals)
+            (xx * w).sum().backward()
+
+        ms = autotune.time_call(step, reps=3, warmup=1)
+        tn, tnnz = (M.n, TT.nnz) if TT is not None else (0, 0)
+        nb = bytes_fwd(M.n, M.nnz, k, 8, tn, tnnz) + bytes_bwd(M.n, M.nnz, k, 8, tn, tnnz)
+        res[name] = {"ms_fwd_bwd": ms, "gbs": nb / (ms * 1e-3) / 1e9,
+                     "levels": P.analyze(M).nlevels}
+    return res
+
+
 def run_extras(P, items, mats, dev, bf_total):
     """Plain level-set baseline, a single-system comparison and the CPU
     oracle, all on rank 0."""
@@ -534,7 +605,15 @@ def run_extras(P, items, mats, dev, bf_total):
             ms = autotune.time_call(lambda: p.solve(b, out=x), reps=5, warmup=2)
             modes[f"{name}:{mode}"] = {"us": 1e3 * ms, "gbs": nb / (ms * 1e-3) / 1e9}
     res["fwd"] = modes
+    # analysis, rewrite and the incremental re-analysis (host-timed, each call synchronises)
+    an_ms = _host_ms(lambda: P.analyze(A))
+    rw_ms = _host_ms(lambda: P.rewrite(A, an.lev, rows, tg))
+    inc_ms = _host_ms(lambda: P.analyze(Lp, prev_lev=an.lev, first_row=int(np.min(rows))))
+    res["preprocess_ms"] = {"analyze": an_ms, "rewrite_1pct": rw_ms, "analyze_incremental_after_rewrite": inc_ms,
+                            "analyze_gbs": (A.nnz * 8 + (A.n + 1) * 4 + A.n * 4) / (an_ms * 1e-3) / 1e9}
     out["single_lap2d_1024_f64"] = res
+    out["powerlaw_4M_f64"] = _single_config(P, S.powerlaw(4_000_000, alpha=2.1, seed=2), dev, 1, autotune)
+    out["lap3d_128_f64_diff_k8"] = _diff_config(P, S.lap3d(128), dev, 8, autotune)
     # --- CPU oracle on the host cores (whole batch, fwd + adjoint, one pass)
     t0 = time.perf_counter()
     nb = 0

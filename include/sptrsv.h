@@ -144,6 +144,20 @@ sptrsv_status sptrsv_analyze(sptrsv_handle handle, const sptrsv_csr *L, int32_t 
                              int32_t *perm, int32_t *level_ptr, int64_t *level_cost,
                              int32_t *nlevels, double stats[6]);
 
+/* The same analysis after a change confined to rows >= first_row (e.g. a
+ * rewrite whose rewritten rows are all >= first_row, Section 2.2: rewriting
+ * row i changes row i only, so every earlier row keeps its level).  lev is
+ * in/out: on entry lev[0 .. first_row) must hold the levels of those rows
+ * (e.g. from sptrsv_analyze of the matrix before the change); the rows from
+ * 32 * floor(first_row / 32) on are recomputed, then perm, level_ptr,
+ * level_cost, *nlevels and stats as sptrsv_analyze.  first_row outside
+ * [0, n] is SPTRSV_EINVAL; first_row = 0 is sptrsv_analyze.  The results
+ * equal sptrsv_analyze's when the entry levels are right; wrong entry levels
+ * are not detected.  Synchronises.                                          */
+sptrsv_status sptrsv_analyze_incremental(sptrsv_handle handle, const sptrsv_csr *L, int32_t first_row,
+                                         int32_t *lev, int32_t *perm, int32_t *level_ptr,
+                                         int64_t *level_cost, int32_t *nlevels, double stats[6]);
+
 /* ----------------------------------------------------------------- rewrite */
 /* Equation rewriting (Section 2.2) by row substitution.  rows[q] (device,
  * nrows entries) is rewritten towards target level targets[q] (device; NULL

@@ -117,7 +117,11 @@ class Analysis:
     STAT_NAMES = ("alc", "arl", "air", "cv_cost", "cv_rows", "thin_threshold")
 
 
-def analyze(A: Matrix) -> Analysis:
+def analyze(A: Matrix, prev_lev: torch.Tensor | None = None, first_row: int = 0) -> Analysis:
+    """Level analysis (sptrsv_analyze).  With prev_lev and first_row > 0 the
+    levels of rows before first_row are taken from prev_lev and only the rest
+    are recomputed (sptrsv_analyze_incremental): use it after a change that
+    left those rows alone, e.g. a rewrite of rows >= first_row."""
     dev = A.row_ptr.device
     n = A.n
     lev = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
@@ -126,8 +130,14 @@ def analyze(A: Matrix) -> Analysis:
     cost = torch.empty(max(n, 1), dtype=torch.int64, device=dev)
     nl = C.c_int32(0)
     st = (C.c_double * 6)()
-    L.check(L.lib().sptrsv_analyze(handle().h, C.byref(A.desc()), _ptr(lev), _ptr(perm), _ptr(lp),
-                                   _ptr(cost), C.byref(nl), st), "sptrsv_analyze")
+    if prev_lev is not None and first_row > 0:
+        lev[:n].copy_(prev_lev[:n])
+        L.check(L.lib().sptrsv_analyze_incremental(handle().h, C.byref(A.desc()), int(first_row), _ptr(lev),
+                                                   _ptr(perm), _ptr(lp), _ptr(cost), C.byref(nl), st),
+                "sptrsv_analyze_incremental")
+    else:
+        L.check(L.lib().sptrsv_analyze(handle().h, C.byref(A.desc()), _ptr(lev), _ptr(perm), _ptr(lp),
+                                       _ptr(cost), C.byref(nl), st), "sptrsv_analyze")
     k = int(nl.value)
     return Analysis(lev[:n], perm[:n], lp[:k + 1], cost[:k], k, np.array(list(st)))
 

@@ -129,6 +129,8 @@ k_levels(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, int32_t
     }
 }
 
+__global__ void k_set_counter(unsigned long long *counter, unsigned long long v) { *counter = v; }
+
 // ---------------------------------------------------------------- max/hist
 __global__ void k_max(const int32_t *lev, int32_t n, int32_t *out)
 {
@@ -248,15 +250,18 @@ cudaError_t launch_validate(const sptrsv_csr &L, long long *out_dev, cudaStream_
 }
 
 cudaError_t launch_levels(const sptrsv_csr &L, int32_t *lev, const Ctl &ctl, long long limit_ns,
-                          const DeviceInfo &di, cudaStream_t s)
+                          const DeviceInfo &di, cudaStream_t s, int64_t first_chunk)
 {
     if (L.n <= 0) return cudaSuccess;
-    cudaError_t e = cudaMemsetAsync(ctl.counters, 0, sizeof(unsigned long long), s);
+    // chunk tickets start at first_chunk: the rows before it keep their levels
+    k_set_counter<<<1, 1, 0, s>>>(ctl.counters, (unsigned long long)first_chunk);
+    cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_levels, kLevThreads, 0);
     if (per_sm < 1) per_sm = 1;
-    const int64_t chunks = ((int64_t)L.n + 31) / 32;
+    const int64_t chunks = ((int64_t)L.n + 31) / 32 - first_chunk;
+    if (chunks <= 0) return cudaSuccess;
     int64_t blocks = (int64_t)per_sm * di.num_sms;
     const int64_t need = (chunks + kLevWarps - 1) / kLevWarps;
     if (blocks > need) blocks = need;

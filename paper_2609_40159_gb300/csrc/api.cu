@@ -228,17 +228,20 @@ sptrsv_status validate_impl(sptrsv_handle h, const sptrsv_csr &L, int32_t *bad_r
 }
 
 // Levels of L into lev (device, n) and their count.  Validates first.
+// Levels of L; rows before 32 * (first_row / 32) keep the levels already in
+// `lev` (incremental recompute after a rewrite that left them unchanged).
 sptrsv_status levels_impl(sptrsv_handle h, const sptrsv_csr &L, int32_t *lev, int32_t *nlevels,
-                          long long spin)
+                          long long spin, int32_t first_row = 0)
 {
     *nlevels = 0;
     sptrsv_status st = validate_impl(h, L, nullptr);
     if (st != SPTRSV_OK || L.n == 0) return st;
     cudaStream_t s = h->stream;
-    cudaError_t e = cudaMemsetAsync(lev, 0xFF, sizeof(int32_t) * (size_t)L.n, s);
+    const int64_t c0 = first_row / 32;
+    cudaError_t e = cudaMemsetAsync(lev + 32 * c0, 0xFF, sizeof(int32_t) * (size_t)(L.n - 32 * c0), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(&h->d_ctl->abort_flag, 0, sizeof(int), s);
     Ctl ctl{h->d_status, &h->d_ctl->abort_flag, &h->d_ctl->ticket};
-    if (e == cudaSuccess) e = launch_levels(L, lev, ctl, spin, h->di, s);
+    if (e == cudaSuccess) e = launch_levels(L, lev, ctl, spin, h->di, s, c0);
     int32_t *dmax = reinterpret_cast<int32_t *>(h->d_scratch + 1);
     if (e == cudaSuccess) e = launch_max(lev, L.n, dmax, s);
     int32_t hm = -1;
@@ -254,9 +257,9 @@ sptrsv_status levels_impl(sptrsv_handle h, const sptrsv_csr &L, int32_t *lev, in
 
 sptrsv_status analyze_into(sptrsv_handle h, const sptrsv_csr &L, int32_t *lev, int32_t *perm,
                            int32_t *level_ptr, int64_t *cost, int32_t *nlevels, double *stats,
-                           long long spin)
+                           long long spin, int32_t first_row = 0)
 {
-    sptrsv_status st = levels_impl(h, L, lev, nlevels, spin);
+    sptrsv_status st = levels_impl(h, L, lev, nlevels, spin, first_row);
     if (st != SPTRSV_OK) return st;
     cudaStream_t s = h->stream;
     cudaError_t e = level_partition(L, lev, *nlevels, perm, level_ptr, cost, s);
@@ -433,6 +436,21 @@ extern "C" sptrsv_status sptrsv_analyze(sptrsv_handle h, const sptrsv_csr *L, in
     }
     double tmp[6];
     return analyze_into(h, *L, lev, perm, level_ptr, level_cost, nlevels, stats ? stats : tmp, kDefaultWaitNs);
+}
+
+extern "C" sptrsv_status sptrsv_analyze_incremental(sptrsv_handle h, const sptrsv_csr *L, int32_t first_row,
+                                                    int32_t *lev, int32_t *perm, int32_t *level_ptr,
+                                                    int64_t *level_cost, int32_t *nlevels, double stats[6])
+{
+    if (!h || !nlevels) return SPTRSV_EINVAL;
+    sptrsv_status st = check_csr(L);
+    if (st != SPTRSV_OK) return st;
+    if (first_row < 0 || first_row > L->n) return SPTRSV_EINVAL;
+    if (L->n == 0) return sptrsv_analyze(h, L, lev, perm, level_ptr, level_cost, nlevels, stats);
+    if (!lev || !perm || !level_ptr || !level_cost) return SPTRSV_EINVAL;
+    double tmp[6];
+    return analyze_into(h, *L, lev, perm, level_ptr, level_cost, nlevels, stats ? stats : tmp, kDefaultWaitNs,
+                        first_row);
 }
 
 // ---------------------------------------------------------------- rewrite

@@ -44,8 +44,10 @@ cudaError_t expand_rows(const int32_t *row_ptr, int32_t n, int32_t *entry_row, c
 // in an int64 (INT64_MAX when the matrix is valid).
 cudaError_t launch_validate(const sptrsv_csr &L, long long *out_dev, cudaStream_t s);
 // Levels (sync-free max-plus over the DAG).  lev must be pre-filled with -1.
+// Levels of rows >= 32 * first_chunk (earlier rows must already hold theirs).
 cudaError_t launch_levels(const sptrsv_csr &L, int32_t *lev, const Ctl &ctl,
-                          long long limit_ns, const DeviceInfo &di, cudaStream_t s);
+                          long long limit_ns, const DeviceInfo &di, cudaStream_t s,
+                          int64_t first_chunk = 0);
 // Level of every row -> max level (nlevels-1) in *maxlev_dev.
 cudaError_t launch_max(const int32_t *lev, int32_t n, int32_t *maxlev_dev, cudaStream_t s);
 // Histogram of rows and costs per level; counts[nlevels], cost[nlevels].

@@ -87,3 +87,44 @@ def test_validate_codes_match_oracle(kind):
     assert st != 0
     with pytest.raises(P._lib.SpTRSVError):
         P.analyze(P.Matrix.from_host(A_h))
+
+
+@pytest.mark.parametrize("gen", ["band", "lap2d_256", "powerlaw"])
+def test_incremental_after_rewrite(gen):
+    """Rewriting changes only the listed rows, so every earlier row keeps its
+    level: the incremental analysis of L' from the first rewritten row,
+    seeded with L's levels, equals the full analysis of L' and the oracle
+    (levels, partition, costs and statistics bit for bit)."""
+    import paper_2609_40159_gb300 as P
+    A_h = {"band": lambda: S.band_random(20_000, 64, 2, 10, seed=21),
+           "lap2d_256": lambda: S.lap2d(256),
+           "powerlaw": lambda: S.powerlaw(100_000, seed=22)}[gen]()
+    A = P.Matrix.from_host(A_h)
+    an = P.analyze(A)
+    rows, tg = S.narrowest_levels_list(an.nlevels, an.level_ptr.cpu().numpy(), an.perm.cpu().numpy(), 0.01, 8)
+    Lp, T = P.rewrite(A, an.lev, rows, tg)
+    first = int(np.min(rows))
+    full = P.analyze(Lp)
+    inc = P.analyze(Lp, prev_lev=an.lev, first_row=first)
+    for f in ("lev", "perm", "level_ptr", "cost"):
+        assert torch.equal(getattr(full, f), getattr(inc, f)), f
+    assert inc.nlevels == full.nlevels and np.array_equal(inc.stats, full.stats)
+    ref = oracle.analyze(oracle.rewrite(A_h, an.lev.cpu().numpy(), rows, tg)[0])
+    assert np.array_equal(inc.lev.cpu().numpy(), ref["lev"])
+    assert np.array_equal(inc.stats, ref["stats"])
+    # first row past the end: nothing recomputed beyond the last partial chunk
+    same = P.analyze(Lp, prev_lev=full.lev, first_row=Lp.n)
+    assert torch.equal(same.lev, full.lev)
+
+
+def test_incremental_bad_first_row():
+    import ctypes as C
+    import paper_2609_40159_gb300 as P
+    from paper_2609_40159_gb300 import _lib as L
+    A = P.Matrix.from_host(S.band_random(1000, 16, 1, 4, seed=3))
+    an = P.analyze(A)
+    nl = C.c_int32(0)
+    st = L.lib().sptrsv_analyze_incremental(P.handle().h, C.byref(A.desc()), A.n + 1, an.lev.data_ptr(),
+                                            an.perm.data_ptr(), an.level_ptr.data_ptr(), an.cost.data_ptr(),
+                                            C.byref(nl), None)
+    assert st == L.SPTRSV_EINVAL
