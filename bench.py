@@ -536,7 +536,7 @@ def _diff_config(P, A_h, dev, k, autotune):
     res = {"n": A.n, "nnz": A.nnz, "k": k, "levels_orig": an.nlevels}
     for name, (M, TT) in {"orig": (A, None), "rewritten": (Lp, T)}.items():
         p = P.Plan(M, TT, transpose=True)
-        vals = M.vals.clone().requires_grad_(True)
+        vals = M.vals.requires_grad_(True)  # the plan's own value tensor
         bb = b.clone().requires_grad_(True)
 
         def step():
@@ -544,6 +544,7 @@ def _diff_config(P, A_h, dev, k, autotune):
             (xx * w).sum().backward()
 
         ms = autotune.time_call(step, reps=3, warmup=1)
+        vals.requires_grad_(False)
         tn, tnnz = (M.n, TT.nnz) if TT is not None else (0, 0)
         nb = bytes_fwd(M.n, M.nnz, k, 8, tn, tnnz) + bytes_bwd(M.n, M.nnz, k, 8, tn, tnnz)
         res[name] = {"ms_fwd_bwd": ms, "gbs": nb / (ms * 1e-3) / 1e9,
