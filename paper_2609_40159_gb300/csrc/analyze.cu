@@ -131,6 +131,15 @@ k_levels(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, int32_t
 
 __global__ void k_set_counter(unsigned long long *counter, unsigned long long v) { *counter = v; }
 
+__global__ void k_count_long(const int32_t *rp, int32_t n, int32_t min_offdiag, unsigned long long *out)
+{
+    unsigned long long c = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        c += (ldro(rp + i + 1) - ldro(rp + i) - 1) > min_offdiag;
+    c = __reduce_add_sync(SPT_FULL_MASK, (unsigned)c);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
+}
+
 // ---------------------------------------------------------------- max/hist
 __global__ void k_max(const int32_t *lev, int32_t n, int32_t *out)
 {
@@ -267,6 +276,15 @@ cudaError_t launch_levels(const sptrsv_csr &L, int32_t *lev, const Ctl &ctl, lon
     if (blocks > need) blocks = need;
     Waiter w{ctl.status, ctl.abort_flag, limit_ns};
     k_levels<<<(int)blocks, kLevThreads, 0, s>>>(L.row_ptr, L.col_idx, L.n, lev, ctl.counters, w);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_count_long(const int32_t *rp, int32_t n, int32_t min_offdiag,
+                              unsigned long long *out_dev, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(out_dev, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess || n <= 0) return e;
+    k_count_long<<<grid_for(n, 256, 1024), 256, 0, s>>>(rp, n, min_offdiag, out_dev);
     return cudaGetLastError();
 }
 

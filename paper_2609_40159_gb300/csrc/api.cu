@@ -44,8 +44,12 @@ sptrsv_status debug_sync(sptrsv_status st, cudaStream_t s, const char *what)
     return from_cuda(e);
 }
 
-int default_rpw(int32_t n, int64_t nnz)
+// Rows per warp from the mean row length; a heavy tail of long rows (more
+// than 0.5 % of the rows with over 32 off-diagonals: one lane would walk
+// each of them alone, on the dependency chain) takes a warp per row.
+int default_rpw(int32_t n, int64_t nnz, int64_t long_rows = 0)
 {
+    if (n > 0 && long_rows * 200 > n) return 1;
     const double avg = n > 0 ? (double)nnz / n : 1.0;
     if (avg <= 12) return 32;
     if (avg <= 24) return 16;
@@ -355,11 +359,16 @@ sptrsv_status ensure_chunks(sptrsv_plan p)
     return SPTRSV_OK;
 }
 
+// Mode from the mean level width: narrow (deep) systems stay on one SM,
+// very wide levels go level by level (row-order sync-free solving keeps
+// only the rows in flight near the wavefront and idles on wide, far-reaching
+// levels: 9x slower than level order on the 3D Laplacian), the rest sync-free.
 int auto_mode(const PlanMat &M)
 {
     if (M.L.n == 0 || M.nlevels == 0) return SPTRSV_MODE_SYNCFREE;
     const double width = (double)M.L.n / M.nlevels;
     if (width < 48.0) return SPTRSV_MODE_BLOCK;
+    if (width >= 2048.0) return SPTRSV_MODE_LEVEL_PERSISTENT;
     return SPTRSV_MODE_SYNCFREE;
 }
 
@@ -492,7 +501,17 @@ extern "C" sptrsv_status sptrsv_plan_create(sptrsv_handle h, const sptrsv_csr *L
     if (st != SPTRSV_OK) { sptrsv_plan_destroy(p); return st; }
     p->have_csc = o.build_transpose != 0;
     p->mode = o.mode != SPTRSV_MODE_AUTO ? o.mode : auto_mode(p->M);
-    p->rpw = valid_rpw(o.rows_per_warp) ? o.rows_per_warp : default_rpw(L->n, L->nnz);
+    if (valid_rpw(o.rows_per_warp)) {
+        p->rpw = o.rows_per_warp;
+    } else {
+        unsigned long long nlong = 0;
+        unsigned long long *d = reinterpret_cast<unsigned long long *>(h->d_scratch + 8);
+        cudaError_t e = launch_count_long(L->row_ptr, L->n, 32, d, h->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&nlong, d, sizeof(nlong), cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) { sptrsv_plan_destroy(p); return from_cuda(e); }
+        p->rpw = default_rpw(L->n, L->nnz, (int64_t)nlong);
+    }
     p->kt = valid_kt(o.rhs_tile) ? o.rhs_tile : 16;
     if (p->mode < SPTRSV_MODE_LEVEL_LAUNCH || p->mode > SPTRSV_MODE_BLOCK) { sptrsv_plan_destroy(p); return SPTRSV_EINVAL; }
     p->grid_level = persistent_grid_level(1, p->dtype == SPTRSV_F64, h->di);

@@ -48,6 +48,9 @@ cudaError_t launch_validate(const sptrsv_csr &L, long long *out_dev, cudaStream_
 cudaError_t launch_levels(const sptrsv_csr &L, int32_t *lev, const Ctl &ctl,
                           long long limit_ns, const DeviceInfo &di, cudaStream_t s,
                           int64_t first_chunk = 0);
+// Number of rows with more than min_offdiag off-diagonals -> *out_dev.
+cudaError_t launch_count_long(const int32_t *rp, int32_t n, int32_t min_offdiag,
+                              unsigned long long *out_dev, cudaStream_t s);
 // Level of every row -> max level (nlevels-1) in *maxlev_dev.
 cudaError_t launch_max(const int32_t *lev, int32_t n, int32_t *maxlev_dev, cudaStream_t s);
 // Histogram of rows and costs per level; counts[nlevels], cost[nlevels].
