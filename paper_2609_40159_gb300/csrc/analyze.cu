@@ -70,6 +70,8 @@ __global__ void k_validate(const int32_t *rp, const int32_t *ci, const void *val
 constexpr int kLevThreads = 256;
 constexpr int kLevWarps = kLevThreads / 32;
 
+constexpr int kLevLong = 32;  // rows with more off-diagonals are walked by the whole warp
+
 __global__ void __launch_bounds__(kLevThreads)
 k_levels(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, int32_t n, int32_t *lev,
          unsigned long long *ticket, Waiter w)
@@ -85,14 +87,19 @@ k_levels(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, int32_t
         if (base >= n) return;
         const int64_t i = base + lane;
         const bool valid = i < n;
-        int p = valid ? ldro(rp + i) : 0;
+        const int a = valid ? ldro(rp + i) : 0;
+        int p = a;
         const int pend = valid ? ldro(rp + i + 1) - 1 : 0;
+        // long rows are left to the cooperative step below
+        const bool islong = pend - a > kLevLong;
         int m = -1;
         bool done = !valid, failed = false;
         my[lane] = -1;
         __syncwarp();
+        WaitClock stall;  // bounds rounds in which no row of the chunk completes
         for (;;) {
-            if (!done) {
+            const unsigned done_before = __ballot_sync(SPT_FULL_MASK, done);
+            if (!done && !islong) {
                 while (p < pend) {
                     const int32_t j = ldro(ci + p);
                     int lj;
@@ -123,8 +130,53 @@ k_levels(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, int32_t
                 }
             }
             __syncwarp();
+            // cooperative step: the lowest pending long row, entries split
+            // over the lanes; retried later if one of them depends on a row
+            // of this chunk that is not done yet (a short row below it, which
+            // progresses, since every long row below it is done)
+            const unsigned pending = __ballot_sync(SPT_FULL_MASK, islong && !done);
+            if (pending) {
+                const int s = __ffs(pending) - 1;
+                const int sa = __shfl_sync(SPT_FULL_MASK, a, s);
+                const int se = __shfl_sync(SPT_FULL_MASK, pend, s);
+                int ms = -1;
+                bool blocked = false;
+                for (int q = sa + lane; q < se && !blocked && !failed; q += 32) {
+                    const int32_t j = ldro(ci + q);
+                    int lj;
+                    if (j >= base) {
+                        lj = my[j - base];
+                        if (lj < 0) blocked = true;
+                    } else {
+                        lj = ld_relaxed(lev + j);
+                        if (lj < 0) {
+                            WaitClock clk;
+                            for (;;) {
+                                lj = ld_relaxed(lev + j);
+                                if (lj >= 0) break;
+                                if (clk.expired(w)) { failed = true; break; }
+                            }
+                        }
+                    }
+                    ms = ms > lj ? ms : lj;
+                }
+                const bool any_blocked = __any_sync(SPT_FULL_MASK, blocked);
+                const bool any_failed = __any_sync(SPT_FULL_MASK, failed);
+                const int mx = __reduce_max_sync(SPT_FULL_MASK, ms);
+                if (!any_blocked && !any_failed && lane == s) {
+                    my[lane] = mx + 1;
+                    st_relaxed(lev + i, mx + 1);
+                    done = true;
+                }
+                __syncwarp();
+            }
             if (__any_sync(SPT_FULL_MASK, failed)) return;
-            if (__all_sync(SPT_FULL_MASK, done)) break;
+            const unsigned done_after = __ballot_sync(SPT_FULL_MASK, done);
+            if (done_after == SPT_FULL_MASK) break;
+            // every round completes a row (the lowest unfinished row of the
+            // chunk has all its in-chunk dependencies done); the bound only
+            // guards that argument
+            if (done_after == done_before && stall.expired(w)) return;
         }
     }
 }
