@@ -78,6 +78,7 @@ def _load(path):
     lib.orc_stats.argtypes = [i32, C.c_int64, i32, i32p, i64p, f64p]
     lib.orc_thin_threshold.argtypes = [C.c_double, C.c_double, C.c_double]
     lib.orc_thin_threshold.restype = C.c_double
+    lib.orc_level_summary.argtypes = [i32, i32p, i32, i32p, i32p, i64p, C.c_double, C.c_void_p, i32p, i64p]
     vp = C.c_void_p
     lib.orc_rewrite.argtypes = [i32, i32p, i32p, f64p, i32p, i32, i32p, vp,
                                 i32p, vp, vp, i32p, vp, vp, C.POINTER(C.c_int32)]
@@ -187,6 +188,23 @@ def stats(n, nnz, nlevels, level_ptr, cost):
 
 def thin_threshold(alc, cv, alpha=1.0):
     return float(_L().orc_thin_threshold(float(alc), float(cv), float(alpha)))
+
+
+def level_summary(A, an, threshold=None):
+    """Thin levels and the per-level row with the fewest dependencies:
+    (thin[nlevels] uint8, pick[nlevels] int32, [thin count, max rows in a
+    thin level, max cost of a thin level]).  threshold defaults to the
+    analysis' thin-level threshold (alpha = 1)."""
+    n, rp, _, _ = _mat(A)
+    nl = int(an["nlevels"])
+    thr = float(an["stats"][5]) if threshold is None else float(threshold)
+    thin = np.zeros(max(nl, 1), np.uint8)
+    pick = np.zeros(max(nl, 1), np.int32)
+    out = np.zeros(3, np.int64)
+    cost = np.ascontiguousarray(an["cost"], dtype=np.int64) if nl else np.zeros(1, np.int64)
+    _L().orc_level_summary(n, rp, nl, _i32(an["level_ptr"]), _i32(an["perm"]) if n else np.zeros(1, np.int32),
+                           cost, thr, thin.ctypes.data_as(C.c_void_p), pick, out)
+    return thin[:nl], pick[:nl], out
 
 
 def analyze(A):

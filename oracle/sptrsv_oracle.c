@@ -198,6 +198,43 @@ double orc_thin_threshold(double alc, double cv, double alpha)
     return alc * (1.0 + alpha * relax);
 }
 
+/* Level summary that the paper's environment observes after every rewrite
+ * (Section 4.1 and Section 4.2, Tables 4-5):
+ *   thin[l]  = 1 when cost[l] < threshold (a thin level: its cost is below
+ *              the thin-level threshold), else 0;
+ *   pick[l]  = the row of level l with the smallest number of dependencies
+ *              (off-diagonals), the smallest row index among equals -- the
+ *              node a rewrite of level l moves (Section 4.2);
+ *   out[0] number of thin levels, out[1] largest row count of a thin level,
+ *   out[2] largest cost of a thin level (0 when there is none).
+ * The cost comparison is in double, as the threshold.                    */
+void orc_level_summary(int32_t n, const int32_t *rp, int32_t nlevels, const int32_t *level_ptr,
+                       const int32_t *perm, const int64_t *cost, double threshold,
+                       uint8_t *thin, int32_t *pick, int64_t *out)
+{
+    (void)n;
+    out[0] = out[1] = out[2] = 0;
+    for (int32_t l = 0; l < nlevels; ++l) {
+        int32_t best = -1, best_deps = 0;
+        for (int32_t q = level_ptr[l]; q < level_ptr[l + 1]; ++q) {
+            const int32_t i = perm[q];
+            const int32_t deps = rp[i + 1] - rp[i] - 1;
+            if (best < 0 || deps < best_deps || (deps == best_deps && i < best)) {
+                best = i;
+                best_deps = deps;
+            }
+        }
+        pick[l] = best;
+        thin[l] = (double)cost[l] < threshold ? 1 : 0;
+        if (thin[l]) {
+            const int64_t rows = level_ptr[l + 1] - level_ptr[l];
+            out[0] += 1;
+            if (rows > out[1]) out[1] = rows;
+            if (cost[l] > out[2]) out[2] = cost[l];
+        }
+    }
+}
+
 /* Scalar statistics of a level table (Tables 4-5, Section 4.1):
  * out[0] ALC  = sum(cost) / L        (average level cost)
  * out[1] ARL  = n / L                (average rows per level)

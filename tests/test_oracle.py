@@ -429,3 +429,73 @@ def test_validate_codes():
     p = B.row_ptr[20]
     B.col_idx[p] = 30
     assert oracle.validate(B)[0] in (oracle.ENOTLOWER, oracle.EUNSORTED)
+
+
+# --------------------------------------------------- environment summary
+def _lap2d_closed_form(N):
+    """Level l of the N x N 5-point lower triangle (natural order): rows
+    (r, c) with r + c = l; deps = [c > 0] + [r > 0]; row cost 2 deps + 1."""
+    L = 2 * N - 1
+    cost = np.zeros(L, np.int64)
+    rows = np.zeros(L, np.int64)
+    pick = np.zeros(L, np.int64)
+    for l in range(L):
+        cells = [(r, l - r) for r in range(N) if 0 <= l - r < N]
+        rows[l] = len(cells)
+        cost[l] = sum(2 * ((c > 0) + (r > 0)) + 1 for r, c in cells)
+        # fewest dependencies: the origin, else a boundary cell (r = 0 has the
+        # smallest index), else the interior cell with the smallest r
+        pick[l] = 0 if l == 0 else (l if l < N else (l - N + 1) * N + N - 1)
+    return cost, rows, pick
+
+
+@pytest.mark.parametrize("N", [2, 6, 17, 40])
+def test_level_summary_lap2d_closed_form(N):
+    A = S.lap2d(N)
+    an = oracle.analyze(A)
+    cost, rows, pick = _lap2d_closed_form(N)
+    alc = cost.sum() / len(cost)
+    cv = cost.std() / cost.mean()  # population
+    thr = alc * (1 + max(0.0, 1 - cv))
+    thin, pk, out = oracle.level_summary(A, an, thr)
+    assert np.array_equal(pk, pick)
+    assert np.array_equal(thin.astype(bool), cost < thr)
+    t = cost < thr
+    assert out[0] == t.sum()
+    assert out[1] == (rows[t].max() if t.any() else 0)
+    assert out[2] == (cost[t].max() if t.any() else 0)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_level_summary_brute_force(seed):
+    """Per-level minimum of (dependencies, row) by a global sort, and the
+    thin set by a direct comparison, on small random systems."""
+    A = S.band_random(300, 24, 0, 6, seed=100 + seed)
+    an = oracle.analyze(A)
+    deps = np.diff(A.row_ptr) - 1
+    lev = an["lev"]
+    order = np.lexsort((np.arange(A.n), deps, lev))  # by level, then deps, then row
+    first = order[np.r_[0, np.flatnonzero(np.diff(lev[order])) + 1]]
+    thr = 0.9 * an["cost"].mean()
+    thin, pk, out = oracle.level_summary(A, an, thr)
+    assert np.array_equal(pk, first)
+    assert np.array_equal(thin.astype(bool), an["cost"] < thr)
+    assert out[0] == int((an["cost"] < thr).sum())
+
+
+def test_level_summary_default_threshold_is_the_papers():
+    A = S.lap2d(9)
+    an = oracle.analyze(A)
+    thin, _, _ = oracle.level_summary(A, an)
+    assert np.array_equal(thin.astype(bool), an["cost"] < an["stats"][5])
+
+
+def test_level_summary_threshold_is_strict():
+    """A level whose cost equals the threshold is not thin (Section 4.1:
+    thin means a cost smaller than the threshold)."""
+    A = S.lap2d(6)
+    an = oracle.analyze(A)
+    cost, _, _ = _lap2d_closed_form(6)
+    thr = float(cost[3])  # 5 * 3 + 1 = 16, also the cost of no other level
+    thin, _, out = oracle.level_summary(A, an, thr)
+    assert not thin[3] and thin[2] and out[0] == int((cost < thr).sum())

@@ -17,6 +17,15 @@ SRC = os.path.join(os.path.dirname(oracle.__file__), "sptrsv_oracle.c")
 
 # (name, original text, planted mistake, pins that must notice it)
 MUTANTS = [
+    ("pick_tie_largest_row", "if (best < 0 || deps < best_deps || (deps == best_deps && i < best)) {",
+     "if (best < 0 || deps < best_deps || (deps == best_deps && i > best)) {",
+     [lambda: P.test_level_summary_lap2d_closed_form(6)]),
+    ("pick_most_deps", "if (best < 0 || deps < best_deps || (deps == best_deps && i < best)) {",
+     "if (best < 0 || deps > best_deps || (deps == best_deps && i < best)) {",
+     [lambda: P.test_level_summary_brute_force(0)]),
+    ("thin_inclusive", "thin[l] = (double)cost[l] < threshold ? 1 : 0;",
+     "thin[l] = (double)cost[l] <= threshold ? 1 : 0;",
+     [P.test_level_summary_threshold_is_strict]),
     ("solve_sign", "s = s - v[p] * x[(int64_t)ci[p] * k + r];",
      "s = s + v[p] * x[(int64_t)ci[p] * k + r];",
      [lambda: P.test_solve_matches_dense_triangular(1, 1)]),
