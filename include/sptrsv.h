@@ -158,6 +158,23 @@ sptrsv_status sptrsv_analyze_incremental(sptrsv_handle handle, const sptrsv_csr 
                                          int32_t *lev, int32_t *perm, int32_t *level_ptr,
                                          int64_t *level_cost, int32_t *nlevels, double stats[6]);
 
+/* What the paper's environment observes after each rewrite (Section 4.1:
+ * thin levels; Section 4.2: the node a move takes from a level is the one
+ * with the fewest dependencies), from an analysis of L:
+ *   perm, level_ptr, level_cost, nlevels  as returned by sptrsv_analyze
+ *                 (device arrays);
+ *   threshold     thin-level threshold (e.g. stats[5] of sptrsv_analyze);
+ *   thin[l]       (device, nlevels bytes) 1 when level_cost[l] < threshold
+ *                 (compared in double), else 0;
+ *   pick[l]       (device, nlevels entries) the row of level l with the
+ *                 fewest off-diagonals, the smallest row among equals;
+ *   summary[3]    (host) number of thin levels, largest row count of a thin
+ *                 level, largest cost of a thin level (0 without thin levels).
+ * SPTRSV_EINVAL for missing arrays or nlevels < 0.  Synchronises.           */
+sptrsv_status sptrsv_level_summary(sptrsv_handle handle, const sptrsv_csr *L, const int32_t *perm,
+                                   const int32_t *level_ptr, const int64_t *level_cost, int32_t nlevels,
+                                   double threshold, uint8_t *thin, int32_t *pick, int64_t summary[3]);
+
 /* ----------------------------------------------------------------- rewrite */
 /* Equation rewriting (Section 2.2) by row substitution.  rows[q] (device,
  * nrows entries) is rewritten towards target level targets[q] (device; NULL

@@ -142,6 +142,24 @@ def analyze(A: Matrix, prev_lev: torch.Tensor | None = None, first_row: int = 0)
     return Analysis(lev[:n], perm[:n], lp[:k + 1], cost[:k], k, np.array(list(st)))
 
 
+def level_summary(A: Matrix, an: Analysis, threshold: float | None = None):
+    """Thin levels (cost below the threshold; default: the analysis' thin-
+    level threshold) and the row with the fewest dependencies of every level
+    (sptrsv_level_summary).  Returns (thin uint8 [nlevels], pick int32
+    [nlevels], numpy [thin count, max rows in a thin level, max cost of a
+    thin level])."""
+    dev = A.row_ptr.device
+    k = an.nlevels
+    thr = float(an.stats[5]) if threshold is None else float(threshold)
+    thin = torch.empty(max(k, 1), dtype=torch.uint8, device=dev)
+    pick = torch.empty(max(k, 1), dtype=torch.int32, device=dev)
+    out = (C.c_int64 * 3)()
+    L.check(L.lib().sptrsv_level_summary(handle().h, C.byref(A.desc()), _ptr(an.perm), _ptr(an.level_ptr),
+                                         _ptr(an.cost), k, thr, _ptr(thin), _ptr(pick), out),
+            "sptrsv_level_summary")
+    return thin[:k], pick[:k], np.array(list(out), dtype=np.int64)
+
+
 def rewrite(A: Matrix, lev: torch.Tensor, rows, targets=None):
     """Row-substitution rewrite (see sptrsv_rewrite); returns (L', T)."""
     dev = A.row_ptr.device

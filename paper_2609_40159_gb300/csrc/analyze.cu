@@ -192,6 +192,47 @@ __global__ void k_count_long(const int32_t *rp, int32_t n, int32_t min_offdiag, 
     if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
 }
 
+// ------------------------------------------------------- level summary
+// One warp per level: the row with the fewest dependencies (smallest row
+// among equals) by a min over 64-bit keys (deps << 32 | row), the thin flag
+// (cost < threshold, compared in double), and the thin-level count, largest
+// row count and largest cost of a thin level (atomics into out[0..2]).
+__global__ void k_level_summary(const int32_t *__restrict__ rp, const int32_t *__restrict__ perm,
+                                const int32_t *__restrict__ level_ptr, const int64_t *__restrict__ cost,
+                                int32_t nlevels, double threshold, uint8_t *thin, int32_t *pick,
+                                unsigned long long *out)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t l = gw; l < nlevels; l += nw) {
+        const int a = ldro(level_ptr + l), e = ldro(level_ptr + l + 1);
+        unsigned long long key = ~0ull;
+        for (int q = a + lane; q < e; q += 32) {
+            const int i = ldro(perm + q);
+            const unsigned long long deps = (unsigned)(ldro(rp + i + 1) - ldro(rp + i) - 1);
+            const unsigned long long k = (deps << 32) | (unsigned)i;
+            key = k < key ? k : key;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long other = __shfl_xor_sync(SPT_FULL_MASK, key, o);
+            key = other < key ? other : key;
+        }
+        if (lane == 0) {
+            pick[l] = (int32_t)(key & 0xffffffffull);
+            const int64_t c = ldro(cost + l);
+            const bool t = (double)c < threshold;
+            thin[l] = t ? 1 : 0;
+            if (t) {
+                atomicAdd(out, 1ull);
+                atomicMax(out + 1, (unsigned long long)(e - a));
+                atomicMax(out + 2, (unsigned long long)c);
+            }
+        }
+    }
+}
+
 // ---------------------------------------------------------------- max/hist
 __global__ void k_max(const int32_t *lev, int32_t n, int32_t *out)
 {
@@ -298,6 +339,19 @@ int grid_for(int64_t work, int threads, int cap = 65535 * 4)
 }
 
 }  // namespace
+
+cudaError_t launch_level_summary(const int32_t *rp, const int32_t *perm, const int32_t *level_ptr,
+                                 const int64_t *cost, int32_t nlevels, double threshold, uint8_t *thin,
+                                 int32_t *pick, unsigned long long *out_dev, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(out_dev, 0, 3 * sizeof(unsigned long long), s);
+    if (e != cudaSuccess || nlevels <= 0) return e;
+    const int64_t blocks = std::min<int64_t>(((int64_t)nlevels + 7) / 8, 152 * 16);
+    k_level_summary<<<(int)blocks, 256, 0, s>>>(rp, perm, level_ptr, cost, nlevels, threshold, thin, pick,
+                                                out_dev);
+    return cudaGetLastError();
+}
+
 
 cudaError_t launch_validate(const sptrsv_csr &L, long long *out_dev, cudaStream_t s)
 {

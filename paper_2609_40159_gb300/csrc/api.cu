@@ -462,6 +462,24 @@ extern "C" sptrsv_status sptrsv_analyze_incremental(sptrsv_handle h, const sptrs
                         first_row);
 }
 
+extern "C" sptrsv_status sptrsv_level_summary(sptrsv_handle h, const sptrsv_csr *L, const int32_t *perm,
+                                              const int32_t *level_ptr, const int64_t *level_cost,
+                                              int32_t nlevels, double threshold, uint8_t *thin,
+                                              int32_t *pick, int64_t summary[3])
+{
+    if (!h || !L || !summary || nlevels < 0) return SPTRSV_EINVAL;
+    if (nlevels > 0 && (!L->row_ptr || !perm || !level_ptr || !level_cost || !thin || !pick)) return SPTRSV_EINVAL;
+    unsigned long long *d = reinterpret_cast<unsigned long long *>(h->d_scratch + 9);
+    unsigned long long host[3] = {0, 0, 0};
+    cudaError_t e = launch_level_summary(L->row_ptr, perm, level_ptr, level_cost, nlevels, threshold, thin, pick,
+                                         d, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(host, d, sizeof(host), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return from_cuda(e);
+    for (int q = 0; q < 3; ++q) summary[q] = (int64_t)host[q];
+    return SPTRSV_OK;
+}
+
 // ---------------------------------------------------------------- rewrite
 extern "C" sptrsv_status sptrsv_rewrite(sptrsv_handle h, const sptrsv_csr *L, const int32_t *lev,
                                         const int32_t *rows, const int32_t *targets, int32_t nrows,

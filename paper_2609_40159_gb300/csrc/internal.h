@@ -48,6 +48,11 @@ cudaError_t launch_validate(const sptrsv_csr &L, long long *out_dev, cudaStream_
 cudaError_t launch_levels(const sptrsv_csr &L, int32_t *lev, const Ctl &ctl,
                           long long limit_ns, const DeviceInfo &di, cudaStream_t s,
                           int64_t first_chunk = 0);
+// Thin flags, fewest-dependency row per level, and (thin count, max rows in
+// a thin level, max cost of a thin level) -> out_dev[0..2].
+cudaError_t launch_level_summary(const int32_t *rp, const int32_t *perm, const int32_t *level_ptr,
+                                 const int64_t *cost, int32_t nlevels, double threshold, uint8_t *thin,
+                                 int32_t *pick, unsigned long long *out_dev, cudaStream_t s);
 // Number of rows with more than min_offdiag off-diagonals -> *out_dev.
 cudaError_t launch_count_long(const int32_t *rp, int32_t n, int32_t min_offdiag,
                               unsigned long long *out_dev, cudaStream_t s);

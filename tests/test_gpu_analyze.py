@@ -6,7 +6,7 @@ import torch
 
 import oracle
 import synthetic as S
-from helpers import cases_small
+from helpers import cases_small, widened
 
 pytestmark = pytest.mark.gpu
 
@@ -128,3 +128,25 @@ def test_incremental_bad_first_row():
                                             an.perm.data_ptr(), an.level_ptr.data_ptr(), an.cost.data_ptr(),
                                             C.byref(nl), None)
     assert st == L.SPTRSV_EINVAL
+
+
+@pytest.mark.parametrize("gen", ["cfg0", "lap2d_1024", "powerlaw_1M", "band_fp32"])
+def test_level_summary_matches_oracle(gen):
+    """Thin flags, the fewest-dependency row of every level and the thin-level
+    summary (the environment's observation after a rewrite) equal the
+    oracle's, at the paper's threshold and at a threshold equal to a level
+    cost (strict comparison)."""
+    import paper_2609_40159_gb300 as P
+    A_h = {"cfg0": lambda: S.band_random(2000, 64, 0, 8, seed=0),
+           "lap2d_1024": lambda: S.lap2d(1024),
+           "powerlaw_1M": lambda: S.powerlaw(1_000_000, seed=5),
+           "band_fp32": lambda: S.band_random(50_000, 300, 4, 16, seed=6).astype(np.float32)}[gen]()
+    A = P.Matrix.from_host(A_h)
+    an = P.analyze(A)
+    ref = oracle.analyze(widened(A_h) if A_h.vals.dtype != np.float64 else A_h)
+    for thr in (None, float(ref["cost"][len(ref["cost"]) // 2])):
+        thin, pick, out = P.level_summary(A, an, thr)
+        rthin, rpick, rout = oracle.level_summary(A_h, ref, thr)
+        assert np.array_equal(thin.cpu().numpy(), rthin)
+        assert np.array_equal(pick.cpu().numpy(), rpick)
+        assert np.array_equal(out, rout)
