@@ -124,3 +124,35 @@ def test_batch_full_size_sampled():
         assert relerr(plan.unpack(x, m).cpu().numpy(), x_ref) <= 1e-5, m
         g_ref = oracle.solve_transpose(widened(refs[m]), plan.unpack(w, m).cpu().numpy())
         assert relerr(plan.unpack(gb, m).cpu().numpy(), g_ref) <= 1e-5, m
+
+
+def test_batch_edge_cases():
+    """Degenerate systems in one batch: n = 1, row counts at and around the
+    32-row group boundary, a diagonal system (no dependencies), a chain
+    (every row depends on the one before: the longest in-group chains), a
+    long-row system (rows beyond the preloaded entries), 1 and 32
+    right-hand sides, forward and adjoint; and an empty batch."""
+    import paper_2609_40159_gb300 as P
+    from helpers import long_row
+    systems = [S.band_random(1, 4, 0, 4, seed=1), S.band_random(31, 8, 0, 6, seed=2),
+               S.band_random(32, 8, 1, 6, seed=3), S.band_random(33, 40, 1, 20, seed=4),
+               S.diagonal(100, seed=5), S.chain(1000, seed=6), long_row(),
+               S.band_random(4097, 700, 10, 40, seed=7)]
+    nrhs = [1, 32, 3, 32, 5, 32, 2, 9]
+    rng = np.random.default_rng(8)
+    mats = [P.Matrix.from_host(A) for A in systems]
+    plan = P.BatchPlan(mats, None, nrhs, transpose=True)
+    bs = [rng.uniform(-1, 1, (A.n, k)) for A, k in zip(systems, nrhs)]
+    b = torch.cat([torch.as_tensor(v).reshape(-1) for v in bs]).cuda()
+    for tile in (1, 8):
+        plan.set_geometry(rhs_tile=tile)
+        x = plan.solve(b)
+        gb = plan.solve_transpose(b)
+        assert P.handle().status() == 0
+        for m, A in enumerate(systems):
+            assert relerr(plan.unpack(x, m).cpu().numpy(), oracle.solve(A, bs[m])) <= TOL[np.float64], (tile, m)
+            assert relerr(plan.unpack(gb, m).cpu().numpy(), oracle.solve_transpose(A, bs[m])) <= TOL[np.float64], (tile, m)
+    empty = P.BatchPlan([], None, [], transpose=True)
+    z = torch.empty(0, dtype=torch.float32, device="cuda")
+    empty.solve(z)
+    assert P.handle().status() == 0
