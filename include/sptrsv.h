@@ -175,6 +175,16 @@ sptrsv_status sptrsv_level_summary(sptrsv_handle handle, const sptrsv_csr *L, co
                                    const int32_t *level_ptr, const int64_t *level_cost, int32_t nlevels,
                                    double threshold, uint8_t *thin, int32_t *pick, int64_t summary[3]);
 
+/* At = A^T for a square CSR matrix A (n x n): At->row_ptr (n+1),
+ * At->col_idx and At->vals (nnz each, A's dtype) are caller-allocated
+ * device arrays; columns come out strictly increasing inside every row.
+ * The transpose of an upper-triangular matrix U whose rows store the
+ * diagonal first is a lower-triangular matrix in this library's layout, so
+ * U x = b is solved as the transpose solve of a plan for U^T (the paper's
+ * preconditioner use needs both triangles).  Validates nothing beyond the
+ * pointers (validate the result).  Synchronises.                           */
+sptrsv_status sptrsv_transpose(sptrsv_handle handle, const sptrsv_csr *A, sptrsv_csr_out *At);
+
 /* ----------------------------------------------------------------- rewrite */
 /* Equation rewriting (Section 2.2) by row substitution.  rows[q] (device,
  * nrows entries) is rewritten towards target level targets[q] (device; NULL

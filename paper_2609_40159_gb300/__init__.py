@@ -8,10 +8,11 @@ touch the GPU; the first call that needs the library loads
 """
 from . import _lib
 from ._lib import SpTRSVError
-from .api import Analysis, BatchPlan, Handle, Matrix, Plan, analyze, handle, level_summary, rewrite, validate
+from .api import (Analysis, BatchPlan, Handle, Matrix, Plan, UpperPlan, analyze, handle, level_summary, rewrite,
+                  transpose, validate)
 from .autograd import BatchSpTRSVFunction, SpTRSVFunction, batch_solve, solve
 
 __all__ = [
     "_lib", "SpTRSVError", "Analysis", "BatchPlan", "Handle", "Matrix", "Plan", "analyze", "handle", "rewrite",
-    "validate", "level_summary", "SpTRSVFunction", "BatchSpTRSVFunction", "solve", "batch_solve",
+    "validate", "level_summary", "transpose", "UpperPlan", "SpTRSVFunction", "BatchSpTRSVFunction", "solve", "batch_solve",
 ]

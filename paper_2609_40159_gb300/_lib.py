@@ -86,6 +86,7 @@ _SIGS = {
     "sptrsv_validate": [sptrsv_handle, C.POINTER(sptrsv_csr), _PI32],
     "sptrsv_analyze": [sptrsv_handle, C.POINTER(sptrsv_csr), _P, _P, _P, _P, _PI32,
                        C.POINTER(C.c_double)],
+    "sptrsv_transpose": [sptrsv_handle, C.POINTER(sptrsv_csr), C.POINTER(sptrsv_csr_out)],
     "sptrsv_level_summary": [sptrsv_handle, C.POINTER(sptrsv_csr), _P, _P, _P, _I32, C.c_double, _P, _P, _PI64],
     "sptrsv_analyze_incremental": [sptrsv_handle, C.POINTER(sptrsv_csr), _I32, _P, _P, _P, _P, _PI32,
                                    C.POINTER(C.c_double)],

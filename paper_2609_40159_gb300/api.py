@@ -160,6 +160,45 @@ def level_summary(A: Matrix, an: Analysis, threshold: float | None = None):
     return thin[:k], pick[:k], np.array(list(out), dtype=np.int64)
 
 
+def transpose(A: Matrix) -> Matrix:
+    """A^T of a square CSR matrix (sptrsv_transpose); the result's columns
+    are strictly increasing inside every row."""
+    dev = A.row_ptr.device
+    rp = torch.empty(A.n + 1, dtype=torch.int32, device=dev)
+    ci = torch.empty(max(A.nnz, 1), dtype=torch.int32, device=dev)
+    v = torch.empty(max(A.nnz, 1), dtype=A.dtype, device=dev)
+    out = L.sptrsv_csr_out(_ptr(rp), _ptr(ci), _ptr(v))
+    L.check(L.lib().sptrsv_transpose(handle().h, C.byref(A.desc()), C.byref(out)), "sptrsv_transpose")
+    return Matrix(rp, ci[:A.nnz], v[:A.nnz])
+
+
+class UpperPlan:
+    """U x = b for an upper-triangular CSR matrix U whose rows store the
+    diagonal first: a plan for the lower-triangular U^T, solved by its
+    transpose solve (and U^T x = b by its forward solve).  The plan holds
+    U^T built from U's values at creation; after changing U's values call
+    refresh()."""
+
+    def __init__(self, U: Matrix, mode="auto", rows_per_warp=0, rhs_tile=0):
+        self.U = U
+        self.Ut = transpose(U)
+        self.plan = Plan(self.Ut, None, mode=mode, rows_per_warp=rows_per_warp, rhs_tile=rhs_tile,
+                         transpose=True)
+
+    def refresh(self):
+        """Re-read U's values (the pattern must be unchanged)."""
+        Ut = transpose(self.U)
+        self.Ut.vals.copy_(Ut.vals)
+
+    def solve(self, b, out=None):
+        """x = U^{-1} b."""
+        return self.plan.solve_transpose(b, out=out)
+
+    def solve_transpose(self, b, out=None):
+        """x = U^{-T} b."""
+        return self.plan.solve(b, out=out)
+
+
 def rewrite(A: Matrix, lev: torch.Tensor, rows, targets=None):
     """Row-substitution rewrite (see sptrsv_rewrite); returns (L', T)."""
     dev = A.row_ptr.device

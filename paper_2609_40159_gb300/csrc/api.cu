@@ -480,6 +480,25 @@ extern "C" sptrsv_status sptrsv_level_summary(sptrsv_handle h, const sptrsv_csr 
     return SPTRSV_OK;
 }
 
+extern "C" sptrsv_status sptrsv_transpose(sptrsv_handle h, const sptrsv_csr *A, sptrsv_csr_out *At)
+{
+    if (!h || !A || !At || A->n < 0 || A->nnz < 0) return SPTRSV_EINVAL;
+    if (A->dtype != SPTRSV_F64 && A->dtype != SPTRSV_F32) return SPTRSV_EINVAL;
+    if (!At->row_ptr || (A->n > 0 && !A->row_ptr)) return SPTRSV_EINVAL;
+    if (A->nnz > 0 && (!A->col_idx || !A->vals || !At->col_idx || !At->vals)) return SPTRSV_EINVAL;
+    cudaStream_t s = h->stream;
+    int32_t *tmap = nullptr;
+    cudaError_t e = cudaMallocAsync(&tmap, sizeof(int32_t) * (size_t)(A->nnz > 0 ? A->nnz : 1), s);
+    if (e == cudaSuccess) e = build_csc(A->row_ptr, A->col_idx, A->n, A->nnz, At->row_ptr, At->col_idx, tmap, s);
+    if (e == cudaSuccess && A->nnz > 0)
+        e = A->dtype == SPTRSV_F64
+                ? csc_values<double>(tmap, (const double *)A->vals, (double *)At->vals, A->nnz, s)
+                : csc_values<float>(tmap, (const float *)A->vals, (float *)At->vals, A->nnz, s);
+    if (tmap) cudaFreeAsync(tmap, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    return from_cuda(e);
+}
+
 // ---------------------------------------------------------------- rewrite
 extern "C" sptrsv_status sptrsv_rewrite(sptrsv_handle h, const sptrsv_csr *L, const int32_t *lev,
                                         const int32_t *rows, const int32_t *targets, int32_t nrows,

@@ -232,3 +232,40 @@ def test_cuda_graph_replay():
             g.replay()
             torch.cuda.synchronize()
             assert relerr(x.cpu().numpy(), oracle.solve(A_h, b.cpu().numpy())) <= 1e-12, mode
+
+
+@pytest.mark.parametrize("mode", ["auto", "level", "syncfree", "block"])
+@pytest.mark.parametrize("k", [1, 4])
+def test_upper_triangular_solve(mode, k):
+    """U x = b for an upper-triangular U (rows store the diagonal first),
+    through the transpose of a lower-triangular plan: against a dense
+    triangular solve and against the oracle's transpose solve of U^T."""
+    import scipy.linalg as sl
+    import scipy.sparse as sp
+    import paper_2609_40159_gb300 as P
+    Lh = S.band_random(3000, 48, 1, 9, seed=31)
+    Ls = sp.csr_matrix((Lh.vals, Lh.col_idx, Lh.row_ptr), shape=(Lh.n, Lh.n))
+    Us = Ls.T.tocsr()
+    Us.sort_indices()  # diagonal first in every row of the upper triangle
+    U = P.Matrix(torch.as_tensor(Us.indptr.astype(np.int32)).cuda(), torch.as_tensor(Us.indices.astype(np.int32)).cuda(),
+                 torch.as_tensor(Us.data).cuda())
+    Ut = P.transpose(U)
+    assert torch.equal(Ut.row_ptr.cpu(), torch.as_tensor(Lh.row_ptr))  # U^T = L exactly
+    assert torch.equal(Ut.col_idx.cpu(), torch.as_tensor(Lh.col_idx))
+    assert torch.equal(Ut.vals.cpu(), torch.as_tensor(Lh.vals))
+    up = P.UpperPlan(U, mode=mode)
+    b = S.rhs(Lh.n, k, seed=32)
+    x = up.solve(torch.as_tensor(b).cuda()).cpu().numpy()
+    assert P.handle().status() == 0
+    assert relerr(x, sl.solve_triangular(Us.toarray(), b, lower=False)) <= TOL[np.float64]
+    assert relerr(x, oracle.solve_transpose(Lh, b)) <= TOL[np.float64]
+    y = up.solve_transpose(torch.as_tensor(b).cuda()).cpu().numpy()
+    assert relerr(y, oracle.solve(Lh, b)) <= TOL[np.float64]
+
+
+def test_transpose_twice_is_identity():
+    import paper_2609_40159_gb300 as P
+    A = P.Matrix.from_host(S.powerlaw(50_000, seed=33))
+    B = P.transpose(P.transpose(A))
+    for f in ("row_ptr", "col_idx", "vals"):
+        assert torch.equal(getattr(A, f), getattr(B, f)), f
