@@ -85,6 +85,22 @@ def hbm_peak():
         return FALLBACK_HBM, "fallback"
 
 
+def kernel_source_hash():
+    """sha256 of the batched solve kernel's sources with comments and blank
+    lines removed: the DRAM traffic recorded in profiles/traffic.json is used
+    only while the code it was measured on is unchanged."""
+    import hashlib
+    import re
+    h = hashlib.sha256()
+    for fn in ("block.cuh", "batch.cu", "rows.cuh", "common.cuh"):
+        with open(os.path.join(ROOT, "paper_2609_40159_gb300", "csrc", fn)) as fh:
+            text = fh.read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        lines = [re.sub(r"//.*", "", ln).rstrip() for ln in text.splitlines()]
+        h.update("\n".join(ln for ln in lines if ln.strip()).encode())
+    return h.hexdigest()
+
+
 # ----------------------------------------------------------------- clocks
 class Clocks:
     """nvidia-smi samples during the timed region."""
@@ -350,12 +366,7 @@ def main():
         with open(tpath) as f:
             tj = json.load(f)
         key = "fwd" if f_ms >= t_ms else "trans"
-        import hashlib
-        h = hashlib.sha256()
-        for fn in ("block.cuh", "batch.cu", "rows.cuh", "common.cuh"):
-            with open(os.path.join(ROOT, "paper_2609_40159_gb300", "csrc", fn), "rb") as fh:
-                h.update(fh.read())
-        if tj.get("source_sha256") == h.hexdigest() and key in tj:
+        if tj.get("source_sha256") == kernel_source_hash() and key in tj:
             traffic = tj[key]["bytes_per_launch_full_scale"]
     except Exception:
         traffic = None

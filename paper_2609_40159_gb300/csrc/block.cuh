@@ -6,13 +6,14 @@
 
 namespace spt {
 
-// Shared-memory layout (dynamic): ring of `ring` rows x KT solution values,
-// ring of row tags (position of the row held by the slot, -1 = empty),
-// ring of chunk tags, counters {ticket, completed prefix}; the one-lane-
-// per-row path orders its groups with kc shared mbarriers instead of the
-// tags and the prefix.
+// Shared-memory layout (dynamic): kc phase barriers, ring of `ring` rows x
+// KT solution values, per-warp coefficient tables and broadcast buffers,
+// ring of row tags (position of the row held by the slot, -1 = empty), ring
+// of chunk tags, counters {ticket, completed prefix}.  The one-lane-per-row
+// path uses the ring, the coefficient tables, the completed-group counter
+// (single-phase) or the barriers (two-phase); the other path uses the tags.
 template <class T, int KT> struct BlockSmem {
-    uint64_t *bar;  // kc phase barriers: bar[c % kc] completes when group c-1 is done
+    uint64_t *bar;  // kc phase barriers: group g arrives on bar[g % kc]
     volatile T *xr;
     T *coef;   // per active warp: [32][32] in-group coefficients
     T *xbuf;   // per active warp: KT broadcast values

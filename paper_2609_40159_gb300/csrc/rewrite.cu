@@ -313,7 +313,7 @@ int blocks_for(int64_t work, int threads, int cap = 65535 * 4)
 
 }  // namespace
 
-// Host driver; see sptrsv_rewrite in sptrsv.h.  Returns an sptrsv_status.
+// Host side of the rewrite; see sptrsv_rewrite in sptrsv.h.  Returns an sptrsv_status.
 int rewrite_run(const sptrsv_csr &L, const int32_t *lev, const int32_t *rows,
                 const int32_t *targets, int32_t nrows, int64_t *nnz_Lp, int64_t *nnz_T,
                 sptrsv_csr_out *Lp_out, sptrsv_csr_out *T_out, const DeviceInfo &di,

@@ -12,9 +12,12 @@
 //                       its own predecessors' ready flags (ld.acquire /
 //                       st.release), rows of the same group resolve through
 //                       shared memory.
-//   k_block             one thread block per system; flags and recent
-//                       solutions in a shared-memory ring (for deep, narrow
-//                       systems where the cross-SM round trip dominates).
+//   k_block             one thread block per system (one per tile of 8
+//                       right-hand-side columns); recent solutions in a
+//                       shared-memory ring, in-order row groups (for deep,
+//                       narrow systems where the cross-SM round trip
+//                       dominates).
+//   k_csc_values        L's values in CSC order before a transpose solve.
 // Every kernel handles both L x = b (rows in increasing order) and the
 // adjoint L^T g_b = g_x (rows in decreasing order, reading L through its CSC).
 // A rewritten system L' x = b + T b gathers its T row into the same sum.
