@@ -59,3 +59,17 @@ def test_status_codes_match_header():
     src = open(HEADER).read()
     for name, val in re.findall(r"(SPTRSV_E[A-Z]+|SPTRSV_OK)\s*=\s*(\d+)", src):
         assert getattr(_lib, name) == int(val)
+
+
+def test_every_entry_point_rejects_null_arguments():
+    """With NULL handles, plans and descriptors (and zero sizes) every entry
+    point returns SPTRSV_EINVAL before it touches a device (this runs on a
+    machine without a GPU)."""
+    import ctypes as C
+    from paper_2609_40159_gb300 import _lib as L
+    lib = L.lib()
+    for name, sig in L._SIGS.items():
+        if name == "sptrsv_status_string":
+            continue
+        args = [t(0) if t in (C.c_int32, C.c_int64, C.c_double) else None for t in sig]
+        assert getattr(lib, name)(*args) == L.SPTRSV_EINVAL, name
