@@ -435,6 +435,10 @@ def main():
             e1.record(sd)
         torch.cuda.synchronize()
         e2e_ms = e0.elapsed_time(e1) / Ke
+        if dist:
+            tm = torch.tensor([e2e_ms], device=dev)
+            dist.all_reduce(tm, op=dist.ReduceOp.MAX)  # the slowest rank bounds the job
+            e2e_ms = float(tm.item())
         if P.handle().status() != 0:
             raise RuntimeError("device status after the end-to-end run")
         e2e = {"value": world * step_bytes / (e2e_ms * 1e-3) / 1e9, "unit": "GB/s",
