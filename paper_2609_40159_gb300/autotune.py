@@ -1,11 +1,12 @@
 """Autotuner for the solve schedule.
 
 For a single-system plan it times every candidate (mode, rows per warp, rhs
-tile) with CUDA events and keeps the fastest; for a batched plan it picks the
-rows-per-warp of every size class (bucketed average row length and number of
-right-hand sides) by coordinate descent over the classes.  Winners are cached
-in a JSON file keyed by size class (``SPTRSV_TUNE_CACHE`` or
-``~/.cache/sptrsv_gb300/tune.json``).
+tile) with CUDA events and keeps the fastest (winners are cached in a JSON
+file keyed by size class: ``SPTRSV_TUNE_CACHE`` or
+``~/.cache/sptrsv_gb300/tune.json``).  For a batched plan, whose time is a
+makespan, it first sets one right-hand-side tile for every system, then
+refines rows per warp and tile per size class (bucketed average row length
+and number of right-hand sides) by coordinate descent.
 """
 from __future__ import annotations
 

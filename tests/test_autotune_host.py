@@ -1,0 +1,70 @@
+"""Host logic of the batched autotuner on CPU: a stand-in plan whose
+"solve time" is a makespan model of the geometry; the tuner must reach the
+model's optimum (uniform tile first, then per-class refinement) and leave
+the plan on its choice."""
+import numpy as np
+import torch
+
+from paper_2609_40159_gb300 import autotune
+
+
+class _Mat:
+    def __init__(self, n, nnz):
+        self.n, self.nnz = n, nnz
+
+
+class _FakeBatch:
+    def __init__(self, mats, nrhs):
+        self.mats, self.nrhs = mats, nrhs
+        self.rpw = [0] * len(mats)
+        self.tile = [8] * len(mats)
+        self.calls = 0
+
+    def set_geometry(self, rows_per_warp=None, rhs_tile=None):
+        if rows_per_warp is not None:
+            self.rpw = [r if r else self.rpw[m] for m, r in enumerate(rows_per_warp)]
+        if rhs_tile is not None:
+            self.tile = [t if t else self.tile[m] for m, t in enumerate(rhs_tile)]
+
+    def solve(self, b, out=None):
+        self.calls += 1
+        return out
+
+    def model_ms(self):
+        # per system: chain cost grows with the tile, items = ceil(k / tile);
+        # short rows prefer 32 rows per warp (0 = the default, same as 32)
+        cost = []
+        for m, A in enumerate(self.mats):
+            t, r = self.tile[m], self.rpw[m] or 32
+            per_item = A.n * (1 + 0.3 * t) * (1.0 if r == 32 else 1.5)
+            items = -(-self.nrhs[m] // t)
+            cost.append((per_item, items))
+        longest = max(c for c, _ in cost)
+        total = sum(c * i for c, i in cost) / 8.0  # 8 "slots"
+        return max(longest, total)
+
+
+def test_tune_batch_reaches_the_model_optimum(monkeypatch):
+    rng = np.random.default_rng(0)
+    mats = [_Mat(int(n), int(n) * 10) for n in rng.integers(1000, 50_000, size=24)]
+    nrhs = [int(k) for k in rng.integers(1, 33, size=24)]
+    fake = _FakeBatch(mats, nrhs)
+    monkeypatch.setattr(autotune, "time_call", lambda fn, reps=3: (fn(), fake.model_ms())[1])
+    res = autotune.tune_batch(fake, torch.zeros(4), candidates=(8, 16, 32), tiles=(2, 4, 8), reps=1)
+    # the plan is left on the reported choice, and that choice is the best time
+    # seen up to the tuner's 0.5 % hysteresis (it ignores smaller gains as noise)
+    assert abs(fake.model_ms() - res["ms"]) < 1e-9
+    assert res["ms"] <= min(e["ms"] for e in res["log"] if e["ms"] is not None) / 0.995
+    # exhaustive search over uniform geometries cannot beat the tuner
+    best_uniform = float("inf")
+    for t in (2, 4, 8):
+        for r in (8, 16, 32):
+            fake.set_geometry([r] * 24, [t] * 24)
+            best_uniform = min(best_uniform, fake.model_ms())
+    assert res["ms"] <= best_uniform / 0.995
+
+
+def test_batch_classes_bucket_row_length_and_rhs():
+    fake = _FakeBatch([_Mat(100, 1000), _Mat(200, 2000), _Mat(100, 100)], [1, 1, 30])
+    labels = autotune.batch_classes(fake)
+    assert labels[0] == labels[1] and labels[0] != labels[2]
