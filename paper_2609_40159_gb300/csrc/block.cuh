@@ -204,37 +204,6 @@ __device__ __forceinline__ void store_vec(T *dst, const T (&v)[KT])
     }
 }
 
-// A group reading the ring slot of group cj: the slot cannot be reused
-// before every group <= cj + kc - P is complete, so it is safe for
-// cj >= c - kc + P (the tag then tells whether the value is there yet);
-// older groups are complete and read from global memory.
-template <class T, int KT>
-__device__ __forceinline__ bool ring_dep(const BlockSmem<T, KT> &sm, const Rhs<T> &R, int ring,
-                                         int c, int P, int kc, int pj, int j, T vv, T (&acc)[KT],
-                                         const Waiter &w)
-{
-    const int kt = R.k;
-    if ((pj >> 5) < c - kc + P) {
-        const T *xx = R.x + (int64_t)j * R.ld;
-#pragma unroll
-        for (int r = 0; r < KT; ++r)
-            if (r < kt) acc[r] += vv * xx[r];
-        return true;
-    }
-    const int slot = pj % ring;
-    int *tg = const_cast<int *>(sm.tag) + slot;
-    if (ld_acquire_cta_smem(tg) != pj) {
-        WaitClock clk;
-        while (ld_acquire_cta_smem(tg) != pj)
-            if (clk.expired(w)) return false;
-    }
-    const T *xx = const_cast<const T *>(sm.xr) + slot * KT;
-#pragma unroll
-    for (int r = 0; r < KT; ++r)
-        if (r < kt) acc[r] += vv * xx[r];
-    return true;
-}
-
 // In-group dependencies of a 32-row group, solved in registers.  Lane L
 // holds the scaled candidates t_L = (b_L - sum over earlier groups) / L_LL,
 // coef[s * 32 + L] = L_Ls / L_LL for every in-group dependency s < L (bit s

@@ -47,10 +47,6 @@ __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long
     asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
 }
-__device__ __forceinline__ void red_release_add(unsigned long long *p, unsigned long long v)
-{
-    asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
 
 // CTA-scope release/acquire on shared memory (ring tags of the block mode).
 __device__ __forceinline__ int ld_acquire_cta_smem(const int *p)
