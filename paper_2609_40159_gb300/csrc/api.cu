@@ -9,11 +9,19 @@
 #include <numeric>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "solve.cuh"
 
 using namespace spt;
 
 namespace {
+
+// Named NVTX range for a profiler timeline (no cost without a tool attached).
+struct Range {
+    explicit Range(const char *name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+};
 constexpr long long kDefaultWaitNs = 10ll * 1000 * 1000 * 1000;  // 10 s
 
 bool debug_mode()
@@ -433,6 +441,7 @@ extern "C" sptrsv_status sptrsv_analyze(sptrsv_handle h, const sptrsv_csr *L, in
                                         int32_t *perm, int32_t *level_ptr, int64_t *level_cost,
                                         int32_t *nlevels, double stats[6])
 {
+    Range range("sptrsv_analyze");
     if (!h || !nlevels) return SPTRSV_EINVAL;
     sptrsv_status st = check_csr(L);
     if (st != SPTRSV_OK) return st;
@@ -451,6 +460,7 @@ extern "C" sptrsv_status sptrsv_analyze_incremental(sptrsv_handle h, const sptrs
                                                     int32_t *lev, int32_t *perm, int32_t *level_ptr,
                                                     int64_t *level_cost, int32_t *nlevels, double stats[6])
 {
+    Range range("sptrsv_analyze_incremental");
     if (!h || !nlevels) return SPTRSV_EINVAL;
     sptrsv_status st = check_csr(L);
     if (st != SPTRSV_OK) return st;
@@ -467,6 +477,7 @@ extern "C" sptrsv_status sptrsv_level_summary(sptrsv_handle h, const sptrsv_csr 
                                               int32_t nlevels, double threshold, uint8_t *thin,
                                               int32_t *pick, int64_t summary[3])
 {
+    Range range("sptrsv_level_summary");
     if (!h || !L || !summary || nlevels < 0) return SPTRSV_EINVAL;
     if (nlevels > 0 && (!L->row_ptr || !perm || !level_ptr || !level_cost || !thin || !pick)) return SPTRSV_EINVAL;
     unsigned long long *d = reinterpret_cast<unsigned long long *>(h->d_scratch + 9);
@@ -482,6 +493,7 @@ extern "C" sptrsv_status sptrsv_level_summary(sptrsv_handle h, const sptrsv_csr 
 
 extern "C" sptrsv_status sptrsv_transpose(sptrsv_handle h, const sptrsv_csr *A, sptrsv_csr_out *At)
 {
+    Range range("sptrsv_transpose");
     if (!h || !A || !At || A->n < 0 || A->nnz < 0) return SPTRSV_EINVAL;
     if (A->dtype != SPTRSV_F64 && A->dtype != SPTRSV_F32) return SPTRSV_EINVAL;
     if (!At->row_ptr || (A->n > 0 && !A->row_ptr)) return SPTRSV_EINVAL;
@@ -505,6 +517,7 @@ extern "C" sptrsv_status sptrsv_rewrite(sptrsv_handle h, const sptrsv_csr *L, co
                                         int64_t *nnz_Lp, int64_t *nnz_T, sptrsv_csr_out *Lp_out,
                                         sptrsv_csr_out *T_out)
 {
+    Range range("sptrsv_rewrite");
     if (!h || nrows < 0) return SPTRSV_EINVAL;
     sptrsv_status st = check_csr(L);
     if (st != SPTRSV_OK) return st;
@@ -518,6 +531,7 @@ extern "C" sptrsv_status sptrsv_rewrite(sptrsv_handle h, const sptrsv_csr *L, co
 extern "C" sptrsv_status sptrsv_plan_create(sptrsv_handle h, const sptrsv_csr *L, const sptrsv_csr *T,
                                             const sptrsv_plan_opts *opts, sptrsv_plan *plan)
 {
+    Range range("sptrsv_plan_create");
     if (!h || !plan) return SPTRSV_EINVAL;
     *plan = nullptr;
     sptrsv_status st = check_csr(L);
@@ -612,6 +626,7 @@ extern "C" sptrsv_status sptrsv_plan_set(sptrsv_plan p, int32_t mode, int32_t ro
 
 extern "C" sptrsv_status sptrsv_solve(sptrsv_plan p, const void *b, void *x, int32_t nrhs, int64_t ld)
 {
+    Range range("sptrsv_solve");
     if (!p || p->batched) return SPTRSV_EINVAL;
     return p->dtype == SPTRSV_F64 ? solve_impl<double>(p, b, x, nrhs, ld, false)
                                   : solve_impl<float>(p, b, x, nrhs, ld, false);
@@ -619,6 +634,7 @@ extern "C" sptrsv_status sptrsv_solve(sptrsv_plan p, const void *b, void *x, int
 
 extern "C" sptrsv_status sptrsv_solve_transpose(sptrsv_plan p, const void *gx, void *gb, int32_t nrhs, int64_t ld)
 {
+    Range range("sptrsv_solve_transpose");
     if (!p || p->batched) return SPTRSV_EINVAL;
     return p->dtype == SPTRSV_F64 ? solve_impl<double>(p, gx, gb, nrhs, ld, true)
                                   : solve_impl<float>(p, gx, gb, nrhs, ld, true);
@@ -627,6 +643,7 @@ extern "C" sptrsv_status sptrsv_solve_transpose(sptrsv_plan p, const void *gx, v
 extern "C" sptrsv_status sptrsv_grad_vals(sptrsv_plan p, const void *gb, const void *x, int32_t nrhs,
                                           int64_t ld, void *gvals)
 {
+    Range range("sptrsv_grad_vals");
     if (!p || p->batched) return SPTRSV_EINVAL;
     if (p->M.L.n == 0) return SPTRSV_OK;
     if (!gb || !x || !gvals || nrhs < 1 || ld < nrhs) return SPTRSV_EINVAL;
@@ -640,6 +657,7 @@ extern "C" sptrsv_status sptrsv_grad_vals(sptrsv_plan p, const void *gb, const v
 
 extern "C" sptrsv_status sptrsv_tt_apply(sptrsv_plan p, const void *gbp, void *gb, int32_t nrhs, int64_t ld)
 {
+    Range range("sptrsv_tt_apply");
     if (!p || p->batched) return SPTRSV_EINVAL;
     if (p->M.L.n == 0) return SPTRSV_OK;
     if (!gbp || !gb || nrhs < 1 || ld < nrhs) return SPTRSV_EINVAL;
@@ -724,6 +742,7 @@ extern "C" sptrsv_status sptrsv_batch_plan_create(sptrsv_handle h, int32_t nmat,
                                                   const sptrsv_csr *Ts, const int32_t *nrhs,
                                                   const sptrsv_plan_opts *opts, sptrsv_plan *plan)
 {
+    Range range("sptrsv_batch_plan_create");
     if (!h || !plan || nmat < 0 || (nmat > 0 && (!Ls || !nrhs))) return SPTRSV_EINVAL;
     *plan = nullptr;
     sptrsv_plan p = new (std::nothrow) sptrsv_plan_st;
@@ -873,11 +892,13 @@ sptrsv_status batch_solve_impl(sptrsv_plan p, const void *b, void *x, bool trans
 
 extern "C" sptrsv_status sptrsv_batch_solve(sptrsv_plan p, const void *b, void *x)
 {
+    Range range("sptrsv_batch_solve");
     return batch_solve_impl(p, b, x, false);
 }
 
 extern "C" sptrsv_status sptrsv_batch_solve_transpose(sptrsv_plan p, const void *gx, void *gb)
 {
+    Range range("sptrsv_batch_solve_transpose");
     return batch_solve_impl(p, gx, gb, true);
 }
 
@@ -914,6 +935,7 @@ extern "C" sptrsv_status sptrsv_batch_trace(sptrsv_plan p, int64_t *trace)
 
 extern "C" sptrsv_status sptrsv_batch_grad_vals(sptrsv_plan p, const void *gb, const void *x, void *gvals)
 {
+    Range range("sptrsv_batch_grad_vals");
     if (!p || !p->batched) return SPTRSV_EINVAL;
     const int32_t nmat = (int32_t)p->mats.size();
     if (nmat == 0) return SPTRSV_OK;
@@ -930,6 +952,7 @@ extern "C" sptrsv_status sptrsv_batch_grad_vals(sptrsv_plan p, const void *gb, c
 
 extern "C" sptrsv_status sptrsv_batch_tt_apply(sptrsv_plan p, const void *gbp, void *gb)
 {
+    Range range("sptrsv_batch_tt_apply");
     if (!p || !p->batched) return SPTRSV_EINVAL;
     const int32_t nmat = (int32_t)p->mats.size();
     if (nmat == 0) return SPTRSV_OK;
