@@ -419,16 +419,85 @@ def test_rewritten_gradient_identity():
     assert np.linalg.norm(gb2 - gb) / np.linalg.norm(gb) <= 1e-12
 
 
+def _validate_fixture():
+    """A valid 60-row system with at least two off-diagonals per row from row
+    10 on (rows are hand-edited below)."""
+    A = S.band_random(60, 8, 2, 4, seed=1)
+    return A
+
+
+def _copy(A):
+    return S.CSR(A.n, A.row_ptr.copy(), A.col_idx.copy(), A.vals.copy())
+
+
+def _drop_row_entries(A, i):
+    """Row i without any entry (row pointers shifted)."""
+    a, e = int(A.row_ptr[i]), int(A.row_ptr[i + 1])
+    rp = A.row_ptr.copy()
+    rp[i + 1:] -= e - a
+    return S.CSR(A.n, rp, np.delete(A.col_idx, np.s_[a:e]), np.delete(A.vals, np.s_[a:e]))
+
+
 def test_validate_codes():
-    A = S.band_random(50, 5, 1, 3, seed=1)
+    """Every status of the validation (Section 2.1: lower triangular, columns
+    sorted, a non-zero diagonal stored last), each for one planted fault with
+    the exact row, and the first-offending rules: the smallest bad row wins,
+    and inside a row the first bad position decides between 'outside [0, i]'
+    and 'not strictly increasing'."""
+    A = _validate_fixture()
+    rp = A.row_ptr
     assert oracle.validate(A) == (oracle.OK, -1)
-    B = S.CSR(A.n, A.row_ptr.copy(), A.col_idx.copy(), A.vals.copy())
-    B.vals[B.row_ptr[10 + 1] - 1] = 0.0
+    # zero diagonal
+    B = _copy(A)
+    B.vals[rp[11] - 1] = 0.0
     assert oracle.validate(B) == (oracle.EDIAG, 10)
-    B = S.CSR(A.n, A.row_ptr.copy(), A.col_idx.copy(), A.vals.copy())
-    p = B.row_ptr[20]
-    B.col_idx[p] = 30
-    assert oracle.validate(B)[0] in (oracle.ENOTLOWER, oracle.EUNSORTED)
+    # a column above the diagonal at the row's first position
+    B = _copy(A)
+    B.col_idx[rp[20]] = 30
+    assert oracle.validate(B) == (oracle.ENOTLOWER, 20)
+    # a negative column
+    B = _copy(A)
+    B.col_idx[rp[21]] = -1
+    assert oracle.validate(B) == (oracle.ENOTLOWER, 21)
+    # two off-diagonals swapped
+    B = _copy(A)
+    B.col_idx[rp[25]], B.col_idx[rp[25] + 1] = B.col_idx[rp[25] + 1], B.col_idx[rp[25]]
+    assert oracle.validate(B) == (oracle.EUNSORTED, 25)
+    # a repeated column is not strictly increasing
+    B = _copy(A)
+    B.col_idx[rp[26] + 1] = B.col_idx[rp[26]]
+    assert oracle.validate(B) == (oracle.EUNSORTED, 26)
+    # the last entry is not the diagonal (sorted, lower, but != i)
+    B = _copy(A)
+    i = next(r for r in range(35, A.n) if B.col_idx[rp[r + 1] - 2] + 1 < r)
+    B.col_idx[rp[i + 1] - 1] = B.col_idx[rp[i + 1] - 2] + 1
+    assert oracle.validate(B) == (oracle.EDIAG, i)
+    # an empty row has no diagonal; decreasing row pointers are invalid
+    assert oracle.validate(_drop_row_entries(A, 40)) == (oracle.EDIAG, 40)
+    B = _copy(A)
+    B.row_ptr[45] = B.row_ptr[44] - 1           # row 44 ends before it starts
+    assert oracle.validate(B) == (oracle.EINVAL, 44)
+    B = _copy(A)
+    B.row_ptr[0] = 1
+    assert oracle.validate(B) == (oracle.EINVAL, 0)
+    # first offending row in row order wins
+    B = _copy(A)
+    B.col_idx[rp[50]] = 55
+    B.vals[rp[13] - 1] = 0.0
+    assert oracle.validate(B) == (oracle.EDIAG, 12)
+    # inside a row, the first bad position decides
+    B = _copy(A)
+    B.col_idx[rp[30]] = 40                      # position 0: above the diagonal
+    B.col_idx[rp[30] + 1] = 0                   # position 1: also decreasing
+    assert oracle.validate(B) == (oracle.ENOTLOWER, 30)
+    B = _copy(A)
+    B.col_idx[rp[33] + 1] = -1                  # position 1: negative AND decreasing: the range
+    assert oracle.validate(B) == (oracle.ENOTLOWER, 33)  # check comes first
+    C = _copy(A)
+    C.col_idx[rp[32] + 1] = C.col_idx[rp[32]]   # position 1 repeated, position 2 above the diagonal
+    C.col_idx[rp[32] + 2] = 99
+    assert rp[33] - rp[32] >= 4                 # row 32 has three off-diagonals and the diagonal
+    assert oracle.validate(C) == (oracle.EUNSORTED, 32)
 
 
 # --------------------------------------------------- environment summary

@@ -72,6 +72,17 @@ MUTANTS = [
     ("solve_rewritten_T_sign", "s = s + tv[p] * b[(int64_t)tci[p] * k + r];",
      "s = s - tv[p] * b[(int64_t)tci[p] * k + r];",
      [P.test_rewrite_worked_example]),
+    ("validate_allows_repeats", "if (p > a && ci[p] <= ci[p - 1])", "if (p > a && ci[p] < ci[p - 1])",
+     [P.test_validate_codes]),
+    ("validate_drops_zero_diag", "if (ci[e - 1] != i || v[e - 1] == 0.0)", "if (ci[e - 1] != i)",
+     [P.test_validate_codes]),
+    ("validate_empty_row_invalid", "return (e < a) ? ORC_EINVAL : ORC_EDIAG;", "return ORC_EINVAL;",
+     [P.test_validate_codes]),
+    ("validate_sorted_before_range", "if (ci[p] < 0 || ci[p] > i) { *bad_row = i; return ORC_ENOTLOWER; }\n"
+     "            if (p > a && ci[p] <= ci[p - 1]) { *bad_row = i; return ORC_EUNSORTED; }",
+     "if (p > a && ci[p] <= ci[p - 1]) { *bad_row = i; return ORC_EUNSORTED; }\n"
+     "            if (ci[p] < 0 || ci[p] > i) { *bad_row = i; return ORC_ENOTLOWER; }",
+     [P.test_validate_codes]),
     ("tt_transposed_operand", "tv[p] * gbp[(int64_t)i * k + r];", "tv[p] * gbp[(int64_t)tci[p] * k + r];",
      [P.test_rewritten_gradient_identity]),
 ]
