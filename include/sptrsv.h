@@ -281,8 +281,13 @@ sptrsv_status sptrsv_batch_tt_apply(sptrsv_plan plan, const void *gbp, void *gb)
  * row plus a control block) in a static device array of this library,
  * sized for at most SPTRSV_NOALLOC_MAX_ROWS rows (4 MiB, held on every
  * device that loads the library until the process exits).
- *   L       matrix descriptor (device arrays, not validated here: validate
- *           it once with sptrsv_validate);
+ *   L       matrix descriptor (device arrays; not fully validated here --
+ *           validate it once with sptrsv_validate -- but the kernel keeps
+ *           every access of a malformed row inside the arrays and reports
+ *           it: row pointers outside [0, nnz] or decreasing are
+ *           SPTRSV_EINVAL, a row whose last entry is not its diagonal
+ *           SPTRSV_EDIAG, a column outside [0, i) SPTRSV_ENOTLOWER; the
+ *           solution is then undefined);
  *   b, x    [n x nrhs] row-major with leading dimension ld (device);
  *   stream  cudaStream_t to run on (NULL = legacy default stream).
  * Returns SPTRSV_ENOTSUP when n > SPTRSV_NOALLOC_MAX_ROWS (nothing is
@@ -306,8 +311,17 @@ sptrsv_status sptrsv_batch_trace(sptrsv_plan plan, int64_t *trace);
 
 /* Test hook for the bounded waits: makes the next solves of `plan` skip
  * publishing row `row` (-1 clears it), so that any row waiting on it gives
- * up after wait_limit_us and the solve reports SPTRSV_ETIMEOUT.            */
+ * up after wait_limit_us and the solve reports SPTRSV_ETIMEOUT.  For a
+ * batched plan rows are counted over the systems in order (row i of system
+ * m is n_0 + ... + n_{m-1} + i).  The level-persistent mode leaves the row
+ * out of its progress counter instead, so every later level waits.         */
 sptrsv_status sptrsv_debug_withhold_row(sptrsv_plan plan, int32_t row);
+
+/* The same hook for the level analysis of `handle` (sptrsv_analyze, the
+ * incremental analysis and plan creation): row `row`'s level is never
+ * published, every wait of those calls gives up after wait_limit_us (> 0)
+ * and they return SPTRSV_ETIMEOUT; row = -1 clears the hook.               */
+sptrsv_status sptrsv_debug_withhold_level(sptrsv_handle handle, int32_t row, int64_t wait_limit_us);
 
 #ifdef __cplusplus
 }

@@ -110,6 +110,7 @@ _SIGS = {
     "sptrsv_batch_grad_vals": [sptrsv_plan, _P, _P, _P],
     "sptrsv_batch_tt_apply": [sptrsv_plan, _P, _P],
     "sptrsv_debug_withhold_row": [sptrsv_plan, _I32],
+    "sptrsv_debug_withhold_level": [sptrsv_handle, _I32, _I64],
     "sptrsv_batch_trace": [sptrsv_plan, _PI64],
     "sptrsv_solve_noalloc": [C.POINTER(sptrsv_csr), _P, _P, _I32, _I64, _P],
 }

@@ -76,6 +76,12 @@ class Handle:
         """Synchronise and return (and clear) the device status word."""
         return int(L.lib().sptrsv_get_status(self.h))
 
+    def withhold_level(self, row: int, wait_limit_us: int = 0):
+        """Test hook of the bounded waits of the level analysis (see
+        sptrsv_debug_withhold_level); row = -1 clears it."""
+        L.check(L.lib().sptrsv_debug_withhold_level(self.h, int(row), int(wait_limit_us)),
+                "sptrsv_debug_withhold_level")
+
     def __del__(self):
         try:
             if getattr(self, "h", None):
@@ -311,12 +317,31 @@ def _per_system(v, m):
 
 class BatchPlan:
     """One plan over many independent systems; right-hand sides, solutions
-    and gradients are packed (see sptrsv_batch_plan_create)."""
+    and gradients are packed (see sptrsv_batch_plan_create).
+
+    The plan copies the systems' values, at creation, into ONE packed tensor
+    ``self.vals`` (system m's values are ``vals[vals_offset[m]:vals_offset[m+1]]``)
+    and its matrices ``self.mats`` read from slices of it: value changes go
+    through ``self.vals`` (or ``self.mats[m].vals``), and the batched autograd
+    Function differentiates with respect to exactly this tensor."""
 
     def __init__(self, mats, Ts=None, nrhs=None, rows_per_warp=None, transpose=False, wait_limit_us=0,
                  rhs_tile=None):
         nmat = len(mats)
-        self.mats, self.Ts = list(mats), list(Ts) if Ts is not None else [None] * nmat
+        mats = list(mats)
+        if nmat:
+            dt = mats[0].dtype
+            if any(A.dtype != dt for A in mats):
+                raise TypeError("all systems of a batch share one value dtype")
+            self.vals = torch.cat([A.vals.detach().reshape(-1) for A in mats])
+            views, a = [], 0
+            for A in mats:
+                views.append(Matrix(A.row_ptr, A.col_idx, self.vals[a:a + A.nnz]))
+                a += A.nnz
+            mats = views
+        else:
+            self.vals = torch.empty(0, dtype=torch.float32, device="cuda")
+        self.mats, self.Ts = mats, list(Ts) if Ts is not None else [None] * nmat
         self.nrhs = [int(k) for k in (nrhs if nrhs is not None else [1] * nmat)]
         descs = (L.sptrsv_csr * max(nmat, 1))()
         tdescs = (L.sptrsv_csr * max(nmat, 1))()
@@ -393,6 +418,12 @@ class BatchPlan:
         gb = out if out is not None else torch.empty_like(gbp)
         L.check(L.lib().sptrsv_batch_tt_apply(self.p, _ptr(gbp), _ptr(gb)), "sptrsv_batch_tt_apply")
         return gb
+
+    def withhold(self, m: int, i: int):
+        """Test hook of the bounded waits: row i of system m is never
+        published by the next solves (m = -1 clears it)."""
+        row = -1 if m < 0 else int(sum(A.n for A in self.mats[:m])) + int(i)
+        L.check(L.lib().sptrsv_debug_withhold_row(self.p, row))
 
     def trace(self):
         """[nmat, 3] int64: start ns, end ns, SM of every system in the last

@@ -50,6 +50,8 @@ def solve(plan: Plan, b: torch.Tensor, vals: torch.Tensor | None = None) -> torc
 class BatchSpTRSVFunction(torch.autograd.Function):
     @staticmethod
     def forward(ctx, vals_packed, b_packed, plan):
+        if vals_packed.data_ptr() != plan.vals.data_ptr() or vals_packed.numel() != plan.vals.numel():
+            raise ValueError("vals_packed must be the plan's packed value tensor (plan.vals)")
         x = plan.solve(b_packed)
         ctx.plan = plan
         ctx.save_for_backward(x)
@@ -67,8 +69,12 @@ class BatchSpTRSVFunction(torch.autograd.Function):
         return gvals, gb, None
 
 
-def batch_solve(plan: BatchPlan, b_packed: torch.Tensor, vals_packed: torch.Tensor) -> torch.Tensor:
-    """Autograd-aware batched solve.  ``vals_packed`` must be the single
-    tensor whose slices [vals_offset[m], vals_offset[m+1]) are the value
-    arrays the plan's matrices were built on."""
-    return BatchSpTRSVFunction.apply(vals_packed, b_packed, plan)
+def batch_solve(plan: BatchPlan, b_packed: torch.Tensor, vals_packed: torch.Tensor | None = None) -> torch.Tensor:
+    """Autograd-aware batched solve (x_m = L_m^{-1} b_m, or L'_m^{-1}(b_m + T_m b_m)
+    for a rewritten system, every system in one launch).  ``vals_packed``
+    must be the plan's packed value tensor ``plan.vals`` (default), whose
+    slice [vals_offset[m], vals_offset[m+1]) is what system m's solve reads;
+    its gradient is the value gradient of every system on its own (for a
+    rewritten system: L''s) pattern.  The plan needs transpose=True for the
+    backward pass."""
+    return BatchSpTRSVFunction.apply(plan.vals if vals_packed is None else vals_packed, b_packed, plan)

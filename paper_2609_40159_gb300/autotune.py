@@ -145,6 +145,8 @@ def tune_batch(bplan: BatchPlan, b: torch.Tensor, candidates=(8, 16, 32), tiles=
         log.append(dict(step="uniform", rhs_tile=t, ms=ms))
         if ms is not None and ms < best_ms:
             best, best_ms = choice, ms
+    if best is None:
+        raise L.SpTRSVError(L.SPTRSV_ENOTSUP, "tune_batch: no candidate right-hand-side tile fits this batch")
     choice = best
     for _ in range(rounds):
         for c in classes:

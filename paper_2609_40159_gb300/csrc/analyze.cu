@@ -74,7 +74,7 @@ constexpr int kLevLong = 32;  // rows with more off-diagonals are walked by the 
 
 __global__ void __launch_bounds__(kLevThreads)
 k_levels(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, int32_t n, int32_t *lev,
-         unsigned long long *ticket, Waiter w)
+         unsigned long long *ticket, Waiter w, int32_t withhold)
 {
     __shared__ int slev[kLevWarps][32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -125,7 +125,7 @@ k_levels(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, int32_t
                 else if (p >= pend) {
                     const int lv = m + 1;
                     my[lane] = lv;
-                    st_relaxed(lev + i, lv);
+                    if (i != withhold) st_relaxed(lev + i, lv);  // test hook: never published
                     done = true;
                 }
             }
@@ -165,7 +165,7 @@ k_levels(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, int32_t
                 const int mx = __reduce_max_sync(SPT_FULL_MASK, ms);
                 if (!any_blocked && !any_failed && lane == s) {
                     my[lane] = mx + 1;
-                    st_relaxed(lev + i, mx + 1);
+                    if (i != withhold) st_relaxed(lev + i, mx + 1);
                     done = true;
                 }
                 __syncwarp();
@@ -365,7 +365,7 @@ cudaError_t launch_validate(const sptrsv_csr &L, long long *out_dev, cudaStream_
 }
 
 cudaError_t launch_levels(const sptrsv_csr &L, int32_t *lev, const Ctl &ctl, long long limit_ns,
-                          const DeviceInfo &di, cudaStream_t s, int64_t first_chunk)
+                          const DeviceInfo &di, cudaStream_t s, int64_t first_chunk, int32_t withhold)
 {
     if (L.n <= 0) return cudaSuccess;
     // chunk tickets start at first_chunk: the rows before it keep their levels
@@ -381,7 +381,7 @@ cudaError_t launch_levels(const sptrsv_csr &L, int32_t *lev, const Ctl &ctl, lon
     const int64_t need = (chunks + kLevWarps - 1) / kLevWarps;
     if (blocks > need) blocks = need;
     Waiter w{ctl.status, ctl.abort_flag, limit_ns};
-    k_levels<<<(int)blocks, kLevThreads, 0, s>>>(L.row_ptr, L.col_idx, L.n, lev, ctl.counters, w);
+    k_levels<<<(int)blocks, kLevThreads, 0, s>>>(L.row_ptr, L.col_idx, L.n, lev, ctl.counters, w, withhold);
     return cudaGetLastError();
 }
 

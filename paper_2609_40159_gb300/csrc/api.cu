@@ -83,6 +83,9 @@ struct sptrsv_handle_st {
     int *d_status = nullptr;
     PlanCtl *d_ctl = nullptr;
     long long *d_scratch = nullptr;  // validation result, max level, stats
+    // test hook of the level analysis (sptrsv_debug_withhold_level)
+    int32_t dbg_withhold = -1;
+    long long dbg_wait_ns = 0;
 };
 
 struct PlanMat {
@@ -253,7 +256,8 @@ sptrsv_status levels_impl(sptrsv_handle h, const sptrsv_csr &L, int32_t *lev, in
     cudaError_t e = cudaMemsetAsync(lev + 32 * c0, 0xFF, sizeof(int32_t) * (size_t)(L.n - 32 * c0), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(&h->d_ctl->abort_flag, 0, sizeof(int), s);
     Ctl ctl{h->d_status, &h->d_ctl->abort_flag, &h->d_ctl->ticket};
-    if (e == cudaSuccess) e = launch_levels(L, lev, ctl, spin, h->di, s, c0);
+    if (h->dbg_withhold >= 0 && h->dbg_wait_ns > 0) spin = h->dbg_wait_ns;
+    if (e == cudaSuccess) e = launch_levels(L, lev, ctl, spin, h->di, s, c0, h->dbg_withhold);
     int32_t *dmax = reinterpret_cast<int32_t *>(h->d_scratch + 1);
     if (e == cudaSuccess) e = launch_max(lev, L.n, dmax, s);
     int32_t hm = -1;
@@ -676,6 +680,14 @@ extern "C" sptrsv_status sptrsv_debug_withhold_row(sptrsv_plan p, int32_t row)
     return SPTRSV_OK;
 }
 
+extern "C" sptrsv_status sptrsv_debug_withhold_level(sptrsv_handle h, int32_t row, int64_t wait_limit_us)
+{
+    if (!h || (row >= 0 && wait_limit_us <= 0)) return SPTRSV_EINVAL;
+    h->dbg_withhold = row < 0 ? -1 : row;
+    h->dbg_wait_ns = row < 0 ? 0 : wait_limit_us * 1000;
+    return SPTRSV_OK;
+}
+
 // ----------------------------------------------------------------- batched
 namespace {
 bool valid_tile(int t) { return t == 1 || t == 2 || t == 4 || t == 8; }
@@ -882,10 +894,12 @@ sptrsv_status batch_solve_impl(sptrsv_plan p, const void *b, void *x, bool trans
     if (e != cudaSuccess) return from_cuda(e);
     if (p->dtype == SPTRSV_F64)
         e = batch_solve<double>(p->d_mats, p->d_items, p->nitems, p->d_order, (const double *)b, (double *)x,
-                                trans, p->d_ctl, w, p->batch_grid_sz, p->batch_smem, p->d_trace, p->h->stream);
+                                trans, p->d_ctl, w, p->batch_grid_sz, p->batch_smem, p->d_trace, p->withhold,
+                                p->h->stream);
     else
         e = batch_solve<float>(p->d_mats, p->d_items, p->nitems, p->d_order, (const float *)b, (float *)x,
-                               trans, p->d_ctl, w, p->batch_grid_sz, p->batch_smem, p->d_trace, p->h->stream);
+                               trans, p->d_ctl, w, p->batch_grid_sz, p->batch_smem, p->d_trace, p->withhold,
+                                p->h->stream);
     return debug_sync(from_cuda(e), p->h->stream, "batch_solve");
 }
 }  // namespace

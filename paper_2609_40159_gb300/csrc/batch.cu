@@ -26,7 +26,7 @@ __device__ __forceinline__ Sys<T> sys_of(const BatchMat &M)
 
 template <class T, int KT, bool TR>
 __device__ __forceinline__ bool run_one(const BatchMat &M, const BatchItem &I, unsigned char *raw,
-                                        const T *b, T *x, const Waiter &w)
+                                        const T *b, T *x, const Waiter &w, int withhold)
 {
     const int ring = I.kc * I.rpw;
     BlockSmem<T, KT> sm = carve_block_smem<T, KT>(raw, ring, I.kc, I.nw);
@@ -37,7 +37,10 @@ __device__ __forceinline__ bool run_one(const BatchMat &M, const BatchItem &I, u
     R.x = x + M.rhs_off + I.r0;
     R.ld = M.k;
     R.k = I.kt;
-    const bool ok = block_solve_any<T, KT, TR, false>(sys_of<T>(M), R, I.rpw, I.kc, I.P, I.nw, sm, w, -1);
+    // test hook: a withheld row (counted over all systems) is never published
+    const int64_t wh = (int64_t)withhold - M.row_off;
+    const int local = (withhold >= 0 && wh >= 0 && wh < M.n) ? (int)wh : -1;
+    const bool ok = block_solve_any<T, KT, TR, false>(sys_of<T>(M), R, I.rpw, I.kc, I.P, I.nw, sm, w, local);
     __syncthreads();
     release_block_smem<T, KT>(sm, I.kc);
     return ok;
@@ -54,7 +57,7 @@ template <class T, bool TR>
 __global__ void __launch_bounds__(kBatchThreads, kBatchMinBlocks)
 k_batch(const BatchMat *__restrict__ mats, const BatchItem *__restrict__ items, int32_t nitems,
         const int32_t *__restrict__ order, const T *b, T *x, PlanCtl *ctl, Waiter w,
-        long long *trace)
+        long long *trace, int withhold)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ int s_next, s_stop;
@@ -76,10 +79,10 @@ k_batch(const BatchMat *__restrict__ mats, const BatchItem *__restrict__ items, 
             trace[3 * it + 2] = (long long)sm_id();
         }
         switch (I.KT) {
-        case 1: run_one<T, 1, TR>(M, I, smraw, b, x, w); break;
-        case 2: run_one<T, 2, TR>(M, I, smraw, b, x, w); break;
-        case 4: run_one<T, 4, TR>(M, I, smraw, b, x, w); break;
-        default: run_one<T, 8, TR>(M, I, smraw, b, x, w); break;
+        case 1: run_one<T, 1, TR>(M, I, smraw, b, x, w, withhold); break;
+        case 2: run_one<T, 2, TR>(M, I, smraw, b, x, w, withhold); break;
+        case 4: run_one<T, 4, TR>(M, I, smraw, b, x, w, withhold); break;
+        default: run_one<T, 8, TR>(M, I, smraw, b, x, w, withhold); break;
         }
         __syncthreads();
         if (trace && threadIdx.x == 0) trace[3 * it + 1] = (long long)now_ns();
@@ -210,15 +213,17 @@ int batch_grid(size_t smem, const DeviceInfo &di)
 template <class T>
 cudaError_t batch_solve(const BatchMat *mats, const BatchItem *items, int32_t nitems,
                         const int32_t *order, const T *b, T *x, bool trans, PlanCtl *ctl,
-                        const Waiter &w, int grid, size_t smem, long long *trace,
+                        const Waiter &w, int grid, size_t smem, long long *trace, int withhold,
                         cudaStream_t s)
 {
     cudaError_t e = launch_prologue<T>(ctl, s);
     if (e != cudaSuccess || nitems <= 0) return e;
     if (trans)
-        k_batch<T, true><<<grid, kBatchThreads, smem, s>>>(mats, items, nitems, order, b, x, ctl, w, trace);
+        k_batch<T, true><<<grid, kBatchThreads, smem, s>>>(mats, items, nitems, order, b, x, ctl, w, trace,
+                                                            withhold);
     else
-        k_batch<T, false><<<grid, kBatchThreads, smem, s>>>(mats, items, nitems, order, b, x, ctl, w, trace);
+        k_batch<T, false><<<grid, kBatchThreads, smem, s>>>(mats, items, nitems, order, b, x, ctl, w, trace,
+                                                             withhold);
     return cudaGetLastError();
 }
 
@@ -253,7 +258,8 @@ cudaError_t batch_csc_values(const BatchMat *mats, int32_t nmat, cudaStream_t s)
 #define SPT_INST(T)                                                                              \
     template cudaError_t batch_solve<T>(const BatchMat *, const BatchItem *, int32_t,             \
                                         const int32_t *, const T *, T *, bool, PlanCtl *,        \
-                                        const Waiter &, int, size_t, long long *, cudaStream_t); \
+                                        const Waiter &, int, size_t, long long *, int,           \
+                                        cudaStream_t);                                           \
     template cudaError_t batch_grad_vals<T>(const BatchMat *, const RowChunk *, int64_t,         \
                                             const T *, const T *, T *, cudaStream_t);            \
     template cudaError_t batch_tt_apply<T>(const BatchMat *, const RowChunk *, int64_t, int64_t, \

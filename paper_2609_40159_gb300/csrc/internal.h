@@ -45,9 +45,10 @@ cudaError_t expand_rows(const int32_t *row_ptr, int32_t n, int32_t *entry_row, c
 cudaError_t launch_validate(const sptrsv_csr &L, long long *out_dev, cudaStream_t s);
 // Levels (sync-free max-plus over the DAG).  lev must be pre-filled with -1.
 // Levels of rows >= 32 * first_chunk (earlier rows must already hold theirs).
+// withhold >= 0: test hook, that row's level is never published.
 cudaError_t launch_levels(const sptrsv_csr &L, int32_t *lev, const Ctl &ctl,
                           long long limit_ns, const DeviceInfo &di, cudaStream_t s,
-                          int64_t first_chunk = 0);
+                          int64_t first_chunk = 0, int32_t withhold = -1);
 // Thin flags, fewest-dependency row per level, and (thin count, max rows in
 // a thin level, max cost of a thin level) -> out_dev[0..2].
 cudaError_t launch_level_summary(const int32_t *rp, const int32_t *perm, const int32_t *level_ptr,

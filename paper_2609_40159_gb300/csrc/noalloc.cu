@@ -54,7 +54,7 @@ __global__ void k_noalloc_begin(unsigned char *scratch)
 
 template <class T>
 __global__ void __launch_bounds__(kThreads)
-k_noalloc_syncfree(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+k_noalloc_syncfree(int32_t n, int64_t nnz, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
                    const T *__restrict__ v, const T *b, T *x, int64_t ld, int32_t k,
                    unsigned char *scratch)
 {
@@ -75,6 +75,21 @@ k_noalloc_syncfree(int32_t n, const int32_t *__restrict__ rp, const int32_t *__r
         const bool valid = i < n;
         const int a = valid ? ldro(rp + i) : 0;
         const int e = valid ? ldro(rp + i + 1) - 1 : 0;
+        // L is not validated here; the checks that keep every access of a
+        // malformed row in bounds cost a few compares per row and one per
+        // entry: row pointers outside [0, nnz] or decreasing, a row whose
+        // last entry is not its diagonal (or that has none), and (below) a
+        // column outside [0, i) before the diagonal, which is not lower
+        // triangular and could also never complete
+        int bad = 0;
+        if (valid) {
+            if (a < 0 || (int64_t)e >= nnz || e + 1 < a) bad = SPTRSV_EINVAL;
+            else if (e < a || ldro(ci + e) != i) bad = SPTRSV_EDIAG;
+        }
+        if (__any_sync(SPT_FULL_MASK, bad != 0)) {
+            if (bad) { set_status(&ctl->status, bad); st_relaxed(&ctl->abort_flag, 1); }
+            return;
+        }
         const unsigned rows = __ballot_sync(SPT_FULL_MASK, valid);
         for (int r = 0; r < k; ++r) {
             T acc = T(0);
@@ -86,6 +101,12 @@ k_noalloc_syncfree(int32_t n, const int32_t *__restrict__ rp, const int32_t *__r
                 if (open) {
                     while (p < e) {
                         const int j = ldro(ci + p);
+                        if (j < 0 || j >= i) {
+                            set_status(&ctl->status, SPTRSV_ENOTLOWER);
+                            st_relaxed(&ctl->abort_flag, 1);
+                            failed = true;
+                            break;
+                        }
                         T xj;
                         if (j >= base) {
                             if (!((fin >> (j - base)) & 1u)) break;
@@ -176,11 +197,11 @@ extern "C" sptrsv_status sptrsv_solve_noalloc(const sptrsv_csr *L, const void *b
     k_noalloc_begin<<<1, 1, 0, s>>>(d->scratch);
     if (L->dtype == SPTRSV_F64)
         k_noalloc_syncfree<double><<<(int)grid, kThreads, 0, s>>>(
-            L->n, L->row_ptr, L->col_idx, (const double *)L->vals, (const double *)b, (double *)x, ld,
+            L->n, L->nnz, L->row_ptr, L->col_idx, (const double *)L->vals, (const double *)b, (double *)x, ld,
             nrhs, d->scratch);
     else
         k_noalloc_syncfree<float><<<(int)grid, kThreads, 0, s>>>(
-            L->n, L->row_ptr, L->col_idx, (const float *)L->vals, (const float *)b, (float *)x, ld,
+            L->n, L->nnz, L->row_ptr, L->col_idx, (const float *)L->vals, (const float *)b, (float *)x, ld,
             nrhs, d->scratch);
     if (cudaGetLastError() != cudaSuccess) return SPTRSV_ECUDA;
     // wait for the solve and report a bounded wait that gave up

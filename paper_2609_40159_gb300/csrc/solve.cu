@@ -154,10 +154,13 @@ k_level_persistent(Sys<T> A, Sched S, Rhs<T> R, int rpw, SyncArgs sy)
                         if (r < kt) xx[r] = (bb[r] - acc[r]) * rinv;
                 }
             }
+            // test hook: a withheld row is never counted, so that every
+            // later level waits for it until the bounded wait gives up
+            const unsigned held = __ballot_sync(SPT_FULL_MASK, active && sl == 0 && i == sy.withhold);
             __syncwarp();
             if (lane == 0) {
                 __threadfence();
-                atomicAdd(&sy.ctl->progress, (unsigned long long)(hi - lo));
+                atomicAdd(&sy.ctl->progress, (unsigned long long)(hi - lo - __popc(held)));
             }
             if (hi >= q1) break;
             ++l;

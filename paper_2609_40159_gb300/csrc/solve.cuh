@@ -156,7 +156,7 @@ struct BatchItem {
 template <class T>
 cudaError_t batch_solve(const BatchMat *mats, const BatchItem *items, int32_t nitems,
                         const int32_t *order, const T *b, T *x, bool trans, PlanCtl *ctl,
-                        const Waiter &w, int grid, size_t smem, long long *trace,
+                        const Waiter &w, int grid, size_t smem, long long *trace, int withhold,
                         cudaStream_t s);
 // cv[q] = v[tmap[q]]: the values of L in CSC order, so that the transpose
 // solves read them without the indirection (refreshed before every

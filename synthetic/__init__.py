@@ -330,25 +330,27 @@ class BatchItem:
 
 
 def batch_spec(nmat: int = 512, seed: int = 3, n_lo: int = 1000, n_hi: int = 200_000,
-               w_lo: int = 16, w_hi: int = 1024, dtype=np.float32, with_rhs: bool = True):
+               w_lo: int = 16, w_hi: int = 1024, dtype=np.float32, with_rhs: bool = True,
+               k_hi: float = 32.0):
     """Batch of independent lower-triangular systems.
 
     Matrix m uses ``np.random.default_rng(SeedSequence(seed).spawn(nmat)[m])``:
     n ~ logU[n_lo, n_hi], band w ~ logU[w_lo, w_hi], off-diagonals per row
-    ~ U{4..16} capped at min(i, w) in [i-w, i), nrhs = round(logU[1, 32]);
-    odd-indexed matrices are marked for a pre-applied rewrite.
+    ~ U{4..16} capped at min(i, w) in [i-w, i), nrhs = round(logU[1, k_hi])
+    (k_hi = 32 for the benchmark's batch); odd-indexed matrices are marked
+    for a pre-applied rewrite.
     """
     children = np.random.SeedSequence(seed).spawn(nmat)
-    return [_batch_one((m, ss, n_lo, n_hi, w_lo, w_hi, dtype, with_rhs))
+    return [_batch_one((m, ss, n_lo, n_hi, w_lo, w_hi, dtype, with_rhs, k_hi))
             for m, ss in enumerate(children)]
 
 
 def _batch_one(args):
-    m, ss, n_lo, n_hi, w_lo, w_hi, dtype, with_rhs = args
+    m, ss, n_lo, n_hi, w_lo, w_hi, dtype, with_rhs, k_hi = args
     rng = np.random.default_rng(ss)
     n = int(round(math.exp(rng.uniform(math.log(n_lo), math.log(n_hi)))))
     w = int(round(math.exp(rng.uniform(math.log(w_lo), math.log(w_hi)))))
-    k = int(round(math.exp(rng.uniform(0.0, math.log(32.0)))))
+    k = int(round(math.exp(rng.uniform(0.0, math.log(k_hi)))))
     A = band_random(n, w, 4, 16, rng=rng, dtype=dtype)
     b = rhs(n, k, rng=rng, dtype=dtype) if with_rhs else None
     return BatchItem(A, k, w, b, rewritten=(m % 2 == 1))
@@ -364,8 +366,9 @@ def batch_spec_parallel(nmat: int = 512, seed: int = 3, workers: int | None = No
     n_lo, n_hi = kw.get("n_lo", 1000), kw.get("n_hi", 200_000)
     w_lo, w_hi = kw.get("w_lo", 16), kw.get("w_hi", 1024)
     dtype, with_rhs = kw.get("dtype", np.float32), kw.get("with_rhs", True)
+    k_hi = kw.get("k_hi", 32.0)
     children = np.random.SeedSequence(seed).spawn(nmat)
-    jobs = [(m, ss, n_lo, n_hi, w_lo, w_hi, dtype, with_rhs) for m, ss in enumerate(children)]
+    jobs = [(m, ss, n_lo, n_hi, w_lo, w_hi, dtype, with_rhs, k_hi) for m, ss in enumerate(children)]
     workers = workers or min(32, os.cpu_count() or 4)
     with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
         return list(ex.map(_batch_one, jobs, chunksize=4))

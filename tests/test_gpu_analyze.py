@@ -34,6 +34,28 @@ def test_analyze_fp32_same_as_fp64():
     _check(S.band_random(5000, 100, 4, 16, seed=9).astype(np.float32))
 
 
+def test_analysis_bounded_wait_reports_timeout():
+    """A row whose level is never published (test hook): the level analysis
+    gives up after the hook's wait limit with SPTRSV_ETIMEOUT (returned by
+    the call and recorded in the status word), the context stays usable, and
+    the next analysis equals the oracle's again."""
+    import paper_2609_40159_gb300 as P
+    A_h = S.band_random(20_000, 48, 1, 8, seed=12)
+    A = P.Matrix.from_host(A_h)
+    h = P.handle()
+    assert h.status() == 0
+    h.withhold_level(7000, wait_limit_us=20_000)
+    try:
+        with pytest.raises(P.SpTRSVError) as e:
+            P.analyze(A)
+        assert e.value.status == P._lib.SPTRSV_ETIMEOUT
+        assert h.status() == P._lib.SPTRSV_ETIMEOUT
+    finally:
+        h.withhold_level(-1)
+    _check(A_h)
+    assert h.status() == 0
+
+
 @pytest.mark.parametrize("gen", ["lap2d_1024", "lap3d_128", "powerlaw_4M"])
 def test_analyze_full_size(gen):
     A = {"lap2d_1024": lambda: S.lap2d(1024), "lap3d_128": lambda: S.lap3d(128),
@@ -75,10 +97,26 @@ def _broken(kind):
         ci[a], ci[a + 1] = ci[a + 1], ci[a]
     elif kind == "no_diag":
         ci[rp[201] - 1] = 199
+    elif kind == "negative":
+        ci[rp[90]] = -1
+    elif kind == "repeated":
+        ci[rp[120] + 1] = ci[rp[120]]
+    elif kind == "range_before_order":  # one position both negative and decreasing
+        ci[rp[130] + 1] = -5
+    elif kind == "rowptr_decreasing":
+        rp[61] = rp[60] - 1
+    elif kind == "first_row_wins":
+        ci[rp[250]] = 280
+        v[rp[13] - 1] = 0.0
+    elif kind == "empty_row":
+        a, e = int(rp[170]), int(rp[171])
+        rp[171:] -= e - a
+        ci, v = np.delete(ci, np.s_[a:e]), np.delete(v, np.s_[a:e])
     return S.CSR(A.n, rp, ci, v)
 
 
-@pytest.mark.parametrize("kind", ["zero_diag", "upper", "unsorted", "no_diag"])
+@pytest.mark.parametrize("kind", ["zero_diag", "upper", "unsorted", "no_diag", "negative", "repeated",
+                                  "range_before_order", "rowptr_decreasing", "first_row_wins", "empty_row"])
 def test_validate_codes_match_oracle(kind):
     import paper_2609_40159_gb300 as P
     A_h = _broken(kind)

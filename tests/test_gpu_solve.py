@@ -191,8 +191,12 @@ def test_full_size_powerlaw():
         assert relerr(plan.solve(b).cpu().numpy(), x_ref) <= 1e-12, mode
 
 
-@pytest.mark.parametrize("mode", ["syncfree", "block"])
+@pytest.mark.parametrize("mode", ["level", "syncfree", "block"])
 def test_bounded_wait_reports_timeout(mode):
+    """A row that is never published (test hook; the level-persistent mode
+    leaves it out of its progress counter): the solve gives up after the
+    plan's wait limit with SPTRSV_ETIMEOUT, the context stays usable and the
+    next solve is right."""
     import paper_2609_40159_gb300 as P
     A_h = S.chain(5000, seed=1)
     A = P.Matrix.from_host(A_h)
