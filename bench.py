@@ -270,7 +270,9 @@ def main():
 
     tune = None
     if not args.no_tune and not args.ncu:
-        tune = autotune.tune_batch(bplan, b, candidates=(8, 16, 32), tiles=(2, 4, 8), reps=3)
+        # each direction on its own timing: the transpose solve has its own geometry
+        tune = {d: autotune.tune_batch(bplan, b, candidates=(8, 16, 32), tiles=(1, 2, 4, 8), reps=3, direction=d)
+                for d in ("forward", "transpose")}
 
     # algorithmic bytes
     wv = 4
@@ -288,8 +290,9 @@ def main():
         gplan = P.BatchPlan(mats, Ts, nrhs, transpose=True)
         if tune is not None:
             labels = autotune.batch_classes(gplan)
-            gplan.set_geometry([tune["choice"][l]["rows_per_warp"] for l in labels],
-                               [tune["choice"][l]["rhs_tile"] for l in labels])
+            for d, tr in tune.items():
+                gplan.set_geometry([tr["choice"][l]["rows_per_warp"] for l in labels],
+                                   [tr["choice"][l]["rhs_tile"] for l in labels], direction=d)
         for _ in range(2):
             gplan.solve(b, out=x)
             gplan.solve_transpose(w, out=gbp)
@@ -373,6 +376,19 @@ def main():
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                 "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "algorithmic_bytes": dom_bytes, "ms_per_launch": dom_ms}
+    # the second bound: dependency latency.  One hop = the per-row time of a
+    # 1-row-per-level chain through the same kernel (alone on the GPU, one
+    # right-hand side); the batch cannot finish before its deepest system's
+    # chain of levels has been walked at that rate.
+    if rank == 0 and not args.ncu:
+        hop_f, hop_t = chain_hop_ns(P, dev)
+        depth = int(max(lv[1] for lv in levels))
+        hop = hop_f if f_ms >= t_ms else hop_t
+        bound_ms = depth * hop * 1e-6
+        roofline["latency"] = {"t_hop_ns": hop, "t_hop_ns_fwd": hop_f, "t_hop_ns_transpose": hop_t,
+                               "depth": depth, "bound_ms": bound_ms, "frac": bound_ms / dom_ms,
+                               "probe": "chain of 131,072 rows (1 row per level), FP32, 1 RHS, "
+                                        "batched kernel, CUDA events, median of 5"}
 
     # end to end through the C ABI with host buffers: every step copies its
     # inputs from pinned host memory and its results back; two buffer sets
@@ -481,7 +497,8 @@ def main():
             "levels": {"max_orig": int(nlev[:, 0].max()), "max_rewritten": int(nlev[1::2, 1].max()),
                        "sum_orig": int(nlev[:, 0].sum()), "sum_after": int(nlev[:, 1].sum())},
             "preprocess_s": {"analyze": t_an, "rewrite": t_rw, "plan": t_plan, "total": t_prep},
-            "autotune": None if tune is None else {"choice": tune["choice"], "ms": tune["ms"]},
+            "autotune": None if tune is None else {d: {"choice": tr["choice"], "ms": tr["ms"]}
+                                                   for d, tr in tune.items()},
             "roofline": roofline,
             "clocks": clocks,
             "gpu_launches": 7 * K,
@@ -493,6 +510,22 @@ def main():
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def chain_hop_ns(P, dev, n=1 << 17):
+    """Nanoseconds per dependency hop of the batched kernel: a 1-row-per-level
+    chain (row i depends on row i-1 only) solved alone, forward and
+    transpose, per row."""
+    import torch
+    from paper_2609_40159_gb300 import autotune
+    A = P.Matrix.from_host(S.chain(n, seed=1).astype(np.float32), device=dev)
+    bp = P.BatchPlan([A], None, [1], transpose=True)
+    bp.set_geometry(rhs_tile=1)
+    b = torch.rand(n, device=dev, dtype=torch.float32)
+    x = torch.empty_like(b)
+    f = autotune.time_call(lambda: bp.solve(b, out=x), reps=5, warmup=2)
+    t = autotune.time_call(lambda: bp.solve_transpose(b, out=x), reps=5, warmup=2)
+    return f * 1e6 / n, t * 1e6 / n
 
 
 def _host_ms(fn, reps=3):

@@ -262,6 +262,13 @@ sptrsv_status sptrsv_batch_offsets(sptrsv_plan plan, int64_t *rhs_offset, int64_
  * geometry).  Synchronises.                                               */
 sptrsv_status sptrsv_batch_plan_set(sptrsv_plan plan, const int32_t *rows_per_warp,
                                     const int32_t *rhs_tile);
+/* The same for one direction: direction 1 = forward solves only, 2 =
+ * transpose solves only (0 = both, as sptrsv_batch_plan_set).  The forward
+ * and transpose solves of a batch keep separate geometries, since their
+ * dependency structures differ (rows of L vs columns of L); an autotuner
+ * times and sets each on its own.  Synchronises.                          */
+sptrsv_status sptrsv_batch_plan_set_direction(sptrsv_plan plan, int32_t direction,
+                                              const int32_t *rows_per_warp, const int32_t *rhs_tile);
 /* All systems in one persistent launch (plus a tiny reset launch; the
  * transpose solve also gathers the values into CSC order first): no host
  * work per matrix, so the call can be captured in a CUDA graph.            */

@@ -105,6 +105,7 @@ _SIGS = {
                                  _PI32, C.POINTER(sptrsv_plan_opts), C.POINTER(sptrsv_plan)],
     "sptrsv_batch_offsets": [sptrsv_plan, _PI64, _PI64],
     "sptrsv_batch_plan_set": [sptrsv_plan, _PI32, _PI32],
+    "sptrsv_batch_plan_set_direction": [sptrsv_plan, _I32, _PI32, _PI32],
     "sptrsv_batch_solve": [sptrsv_plan, _P, _P],
     "sptrsv_batch_solve_transpose": [sptrsv_plan, _P, _P],
     "sptrsv_batch_grad_vals": [sptrsv_plan, _P, _P, _P],

@@ -366,9 +366,11 @@ class BatchPlan:
         self.vals_offset = np.array(list(vo), dtype=np.int64)
         self.dtype = mats[0].dtype if nmat else torch.float32
 
-    def set_geometry(self, rows_per_warp=None, rhs_tile=None):
+    def set_geometry(self, rows_per_warp=None, rhs_tile=None, direction="both"):
         """Row-group width and right-hand-side columns per work item, per
-        system (list) or for all systems (int); None or 0 keeps the value."""
+        system (list) or for all systems (int); None or 0 keeps the value.
+        direction: "both", "forward" or "transpose" (the two directions keep
+        separate geometries)."""
         nmat = len(self.mats)
 
         def arr(v):
@@ -376,8 +378,9 @@ class BatchPlan:
                 return None
             return (C.c_int32 * max(nmat, 1))(*[_per_system(v, m) for m in range(nmat)])
 
-        L.check(L.lib().sptrsv_batch_plan_set(self.p, arr(rows_per_warp), arr(rhs_tile)),
-                "sptrsv_batch_plan_set")
+        d = {"both": 0, "forward": 1, "transpose": 2}[direction]
+        L.check(L.lib().sptrsv_batch_plan_set_direction(self.p, d, arr(rows_per_warp), arr(rhs_tile)),
+                "sptrsv_batch_plan_set_direction")
 
     def set_rows_per_warp(self, rpw):
         """Row-group width per system (list) or for all systems (int)."""

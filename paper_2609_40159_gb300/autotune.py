@@ -117,26 +117,31 @@ def batch_classes(bplan: BatchPlan):
 
 
 def tune_batch(bplan: BatchPlan, b: torch.Tensor, candidates=(8, 16, 32), tiles=(2, 4, 8), reps=3,
-               rounds=1):
-    """Rows-per-warp and right-hand-side tile of the batched solve.  The
-    batch time is a makespan, so the search first sets one tile width for
-    every system, then refines per size class (coordinate descent: each
-    class tries every candidate of one knob with everything else fixed).
-    A rows-per-warp of 0 keeps the plan's default for that system."""
+               rounds=1, direction="forward"):
+    """Rows-per-warp and right-hand-side tile of the batched solve in one
+    direction ("forward": the solve; "transpose": the transpose solve of
+    the adjoint, which has its own geometry and its own timing).  The batch
+    time is a makespan, so the search first sets one tile width for every
+    system, then refines per size class (coordinate descent: each class
+    tries every candidate of one knob with everything else fixed).  A
+    rows-per-warp of 0 keeps the plan's default for that system."""
+    if direction not in ("forward", "transpose"):
+        raise ValueError("direction must be 'forward' or 'transpose'")
     labels = batch_classes(bplan)
     classes = sorted(set(labels))
     x = torch.empty_like(b)
     log = []
+    run = bplan.solve if direction == "forward" else bplan.solve_transpose
 
     def apply(choice):
-        bplan.set_geometry([choice[l][0] for l in labels], [choice[l][1] for l in labels])
+        bplan.set_geometry([choice[l][0] for l in labels], [choice[l][1] for l in labels], direction=direction)
 
     def measure(choice):
         try:
             apply(choice)
         except L.SpTRSVError:
             return None
-        return time_call(lambda: bplan.solve(b, out=x), reps=reps)
+        return time_call(lambda: run(b, out=x), reps=reps)
 
     best, best_ms = None, float("inf")
     for t in tiles:
@@ -163,4 +168,4 @@ def tune_batch(bplan: BatchPlan, b: torch.Tensor, candidates=(8, 16, 32), tiles=
                 choice[c][knob] = keep
     apply(choice)
     return dict(choice={c: dict(rows_per_warp=v[0], rhs_tile=v[1]) for c, v in choice.items()}, ms=best_ms,
-                log=log)
+                log=log, direction=direction)

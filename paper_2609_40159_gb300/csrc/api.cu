@@ -123,15 +123,27 @@ struct sptrsv_plan_st {
     std::vector<int64_t> rhs_off, vals_off, row_off;
     BatchMat *d_mats = nullptr;
     std::vector<BatchMat> h_mats;
-    std::vector<int32_t> b_rpw, b_tile;  // per system: rows per warp, rhs columns per work item
-    BatchItem *d_items = nullptr;        // work items: (system, rhs column tile) and its geometry
-    int32_t nitems = 0, max_items = 0;
-    int32_t *d_order = nullptr;
+    // work items of each direction ([0] forward, [1] transpose): per system
+    // rows per warp and rhs columns per work item, the items (system, rhs
+    // column tile, geometry), their launch order, shared memory and grid
+    struct Geom {
+        std::vector<int32_t> rpw, tile;
+        BatchItem *d_items = nullptr;
+        int32_t *d_order = nullptr;
+        int32_t nitems = 0;
+        size_t smem = 0;
+        int grid = 0;
+    } geo[2];
+    int32_t max_items = 0;
+    int last_dir = 0;  // direction of the last batched solve (for the trace)
     RowChunk *d_gchunks = nullptr, *d_tchunks = nullptr;  // all 32-row chunks; chunks with T rows
     int64_t n_gchunks = 0, n_tchunks = 0;
+    RowChunk *d_ctiles = nullptr;   // tiles of the CSC value gather: (system, first entry)
+    int64_t n_ctiles = 0;
+    RowChunk *d_fchunks = nullptr;  // every 32-row chunk of the rewritten systems
+    int64_t n_fchunks = 0;
+    void *d_bt = nullptr;           // b + T b of the rewritten systems (packed like b)
     long long *d_trace = nullptr;  // per work item: start ns, end ns, SM of the last batch solve
-    size_t batch_smem = 0;
-    int batch_grid_sz = 0;
 
     template <class P> cudaError_t alloc(P **p, size_t bytes)
     {
@@ -609,8 +621,8 @@ extern "C" sptrsv_status sptrsv_plan_info(sptrsv_plan p, int32_t *nlevels, int32
         }
     }
     if (mode) *mode = p->batched ? SPTRSV_MODE_BLOCK : p->mode;
-    if (rows_per_warp) *rows_per_warp = p->batched ? (p->b_rpw.empty() ? 32 : p->b_rpw[0]) : p->rpw;
-    if (rhs_tile) *rhs_tile = p->batched ? (p->b_tile.empty() ? 4 : p->b_tile[0]) : p->kt;
+    if (rows_per_warp) *rows_per_warp = p->batched ? (p->geo[0].rpw.empty() ? 32 : p->geo[0].rpw[0]) : p->rpw;
+    if (rhs_tile) *rhs_tile = p->batched ? (p->geo[0].tile.empty() ? 4 : p->geo[0].tile[0]) : p->kt;
     return SPTRSV_OK;
 }
 
@@ -699,12 +711,14 @@ int pow2_at_least(int v)
     return k;
 }
 
-// Work items of a batch: every system is split into tiles of at most b_tile
-// right-hand-side columns, each an independent in-order chain solved by one
-// thread block.  Builds the items with their geometry, orders them longest
-// estimated chain first (LPT), and sizes shared memory and the grid.
-sptrsv_status rebuild_items(sptrsv_plan p)
+// Work items of one direction of a batch: every system is split into tiles
+// of at most `tile` right-hand-side columns, each an independent in-order
+// chain solved by one thread block.  Builds the items with their geometry,
+// orders them longest estimated chain first (LPT), and sizes shared memory
+// and the grid.
+sptrsv_status rebuild_items(sptrsv_plan p, int dir)
 {
+    sptrsv_plan_st::Geom &G = p->geo[dir];
     const int32_t nmat = (int32_t)p->mats.size();
     const bool f64 = p->dtype == SPTRSV_F64;
     std::vector<BatchItem> items;
@@ -713,14 +727,14 @@ sptrsv_status rebuild_items(sptrsv_plan p)
     for (int m = 0; m < nmat; ++m) {
         const PlanMat &M = p->mats[m];
         const int k = p->h_mats[m].k;
-        const int tile = p->b_tile[m];
+        const int tile = G.tile[m];
         for (int r0 = 0; r0 < k; r0 += tile) {
             BatchItem I{};
             I.mat = m;
             I.r0 = r0;
             I.kt = std::min(tile, k - r0);
             I.KT = pow2_at_least(I.kt);
-            I.rpw = p->b_rpw[m];
+            I.rpw = G.rpw[m];
             I.nw = std::min(kBatchWarps,
                             block_warps_for(M.nlevels > 0 ? (double)M.L.n / M.nlevels : 1.0, I.rpw));
             block_geometry(I.rpw, I.KT, f64, I.nw, &I.kc, &I.P, kBatchSmemGrow);
@@ -739,13 +753,42 @@ sptrsv_status rebuild_items(sptrsv_plan p)
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return est[x] > est[y]; });
     cudaError_t e = cudaStreamSynchronize(p->h->stream);
     if (e == cudaSuccess && ni > 0)
-        e = cudaMemcpy(p->d_items, items.data(), sizeof(BatchItem) * ni, cudaMemcpyHostToDevice);
+        e = cudaMemcpy(G.d_items, items.data(), sizeof(BatchItem) * ni, cudaMemcpyHostToDevice);
     if (e == cudaSuccess && ni > 0)
-        e = cudaMemcpy(p->d_order, order.data(), sizeof(int32_t) * ni, cudaMemcpyHostToDevice);
+        e = cudaMemcpy(G.d_order, order.data(), sizeof(int32_t) * ni, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return from_cuda(e);
-    p->nitems = ni;
-    p->batch_smem = smem;
-    p->batch_grid_sz = std::min(batch_grid(smem, p->h->di), std::max(ni, 1));
+    G.nitems = ni;
+    G.smem = smem;
+    G.grid = std::min(batch_grid(smem, p->h->di), std::max(ni, 1));
+    return SPTRSV_OK;
+}
+
+// New per-system geometry for the directions in `dirs` (bit 0 forward, bit
+// 1 transpose); values 0 keep the current one.  A geometry that does not fit
+// in shared memory is refused and the previous one kept.
+sptrsv_status set_geometry(sptrsv_plan p, int dirs, const int32_t *rows_per_warp, const int32_t *rhs_tile)
+{
+    const int32_t nmat = (int32_t)p->h_mats.size();
+    for (int m = 0; m < nmat; ++m) {
+        if (rows_per_warp && rows_per_warp[m] != 0 && !valid_rpw(rows_per_warp[m])) return SPTRSV_EINVAL;
+        if (rhs_tile && rhs_tile[m] != 0 && !valid_tile(rhs_tile[m])) return SPTRSV_EINVAL;
+    }
+    for (int d = 0; d < 2; ++d) {
+        if (!((dirs >> d) & 1)) continue;
+        sptrsv_plan_st::Geom &G = p->geo[d];
+        const std::vector<int32_t> old_rpw = G.rpw, old_tile = G.tile;
+        for (int m = 0; m < nmat; ++m) {
+            if (rows_per_warp && rows_per_warp[m]) G.rpw[m] = rows_per_warp[m];
+            if (rhs_tile && rhs_tile[m]) G.tile[m] = rhs_tile[m];
+        }
+        sptrsv_status st = rebuild_items(p, d);
+        if (st == SPTRSV_ENOTSUP) {
+            G.rpw = old_rpw;
+            G.tile = old_tile;
+            if (rebuild_items(p, d) != SPTRSV_OK) return SPTRSV_ECUDA;
+        }
+        if (st != SPTRSV_OK) return st;
+    }
     return SPTRSV_OK;
 }
 }  // namespace
@@ -774,8 +817,10 @@ extern "C" sptrsv_status sptrsv_batch_plan_create(sptrsv_handle h, int32_t nmat,
     p->vals_off.assign((size_t)nmat + 1, 0);
     p->row_off.assign((size_t)nmat + 1, 0);
     p->h_mats.resize((size_t)nmat);
-    p->b_rpw.assign((size_t)nmat, 32);
-    p->b_tile.assign((size_t)nmat, 4);
+    for (int d = 0; d < 2; ++d) {
+        p->geo[d].rpw.assign((size_t)nmat, 32);
+        p->geo[d].tile.assign((size_t)nmat, 4);
+    }
     int64_t ktot = 0;
     for (int m = 0; m < nmat; ++m) {
         sptrsv_status st = check_csr(&Ls[m]);
@@ -803,15 +848,19 @@ extern "C" sptrsv_status sptrsv_batch_plan_create(sptrsv_handle h, int32_t nmat,
         p->rhs_off[m + 1] = p->rhs_off[m] + (int64_t)M.L.n * B.k;
         p->vals_off[m + 1] = p->vals_off[m] + M.L.nnz;
         p->row_off[m + 1] = p->row_off[m] + M.L.n;
-        p->b_rpw[m] = opts && opts[m].rows_per_warp ? opts[m].rows_per_warp : default_rpw(M.L.n, M.L.nnz);
-        if (opts && opts[m].rhs_tile) p->b_tile[m] = opts[m].rhs_tile;
+        for (int d = 0; d < 2; ++d) {
+            p->geo[d].rpw[m] = opts && opts[m].rows_per_warp ? opts[m].rows_per_warp : default_rpw(M.L.n, M.L.nnz);
+            if (opts && opts[m].rhs_tile) p->geo[d].tile[m] = opts[m].rhs_tile;
+        }
         ktot += B.k;
     }
     p->have_csc = want_csc;
     p->max_items = (int32_t)std::max<int64_t>(ktot, 1);  // tiles of one column at most
     e = p->alloc(&p->d_mats, sizeof(BatchMat) * (size_t)(nmat > 0 ? nmat : 1));
-    if (e == cudaSuccess) e = p->alloc(&p->d_items, sizeof(BatchItem) * (size_t)p->max_items);
-    if (e == cudaSuccess) e = p->alloc(&p->d_order, sizeof(int32_t) * (size_t)p->max_items);
+    for (int d = 0; d < 2; ++d) {
+        if (e == cudaSuccess) e = p->alloc(&p->geo[d].d_items, sizeof(BatchItem) * (size_t)p->max_items);
+        if (e == cudaSuccess) e = p->alloc(&p->geo[d].d_order, sizeof(int32_t) * (size_t)p->max_items);
+    }
     if (e == cudaSuccess) e = p->alloc(&p->d_trace, sizeof(long long) * 3 * (size_t)p->max_items);
     if (e == cudaSuccess && nmat > 0)
         e = cudaMemcpy(p->d_mats, p->h_mats.data(), sizeof(BatchMat) * nmat, cudaMemcpyHostToDevice);
@@ -819,7 +868,7 @@ extern "C" sptrsv_status sptrsv_batch_plan_create(sptrsv_handle h, int32_t nmat,
     {
         // chunk tables of the elementwise adjoint kernels: every 32-row chunk,
         // and the chunks whose T-row mask word is non-zero
-        std::vector<RowChunk> g, t;
+        std::vector<RowChunk> g, t, f;
         std::vector<uint32_t> mask;
         e = cudaStreamSynchronize(p->h->stream);  // T-row masks are built on the handle's stream
         for (int m = 0; m < nmat && e == cudaSuccess; ++m) {
@@ -827,6 +876,7 @@ extern "C" sptrsv_status sptrsv_batch_plan_create(sptrsv_handle h, int32_t nmat,
             const int32_t nw = (M.L.n + 31) / 32;
             for (int32_t c = 0; c < nw; ++c) g.push_back(RowChunk{m, 32 * c});
             if (!M.hasT || nw == 0) continue;
+            for (int32_t c = 0; c < nw; ++c) f.push_back(RowChunk{m, 32 * c});
             mask.resize((size_t)nw);
             e = cudaMemcpy(mask.data(), M.d_tmask, sizeof(uint32_t) * nw, cudaMemcpyDeviceToHost);
             for (int32_t c = 0; c < nw && e == cudaSuccess; ++c)
@@ -834,6 +884,25 @@ extern "C" sptrsv_status sptrsv_batch_plan_create(sptrsv_handle h, int32_t nmat,
         }
         p->n_gchunks = (int64_t)g.size();
         p->n_tchunks = (int64_t)t.size();
+        p->n_fchunks = (int64_t)f.size();
+        if (e == cudaSuccess && want_csc) {
+            std::vector<RowChunk> ct;
+            for (int m = 0; m < nmat; ++m)
+                for (int64_t q = 0; q < p->mats[m].L.nnz; q += kCscTile) ct.push_back(RowChunk{m, (int32_t)q});
+            p->n_ctiles = (int64_t)ct.size();
+            if (!ct.empty()) {
+                e = p->alloc(&p->d_ctiles, sizeof(RowChunk) * ct.size());
+                if (e == cudaSuccess)
+                    e = cudaMemcpy(p->d_ctiles, ct.data(), sizeof(RowChunk) * ct.size(), cudaMemcpyHostToDevice);
+            }
+        }
+        if (e == cudaSuccess && !f.empty()) {
+            e = p->alloc(&p->d_fchunks, sizeof(RowChunk) * f.size());
+            if (e == cudaSuccess)
+                e = cudaMemcpy(p->d_fchunks, f.data(), sizeof(RowChunk) * f.size(), cudaMemcpyHostToDevice);
+            if (e == cudaSuccess)
+                e = p->alloc(&p->d_bt, (p->dtype == SPTRSV_F64 ? 8 : 4) * (size_t)std::max<int64_t>(p->rhs_off[nmat], 1));
+        }
         if (e == cudaSuccess) e = p->alloc(&p->d_gchunks, sizeof(RowChunk) * std::max<size_t>(g.size(), 1));
         if (e == cudaSuccess) e = p->alloc(&p->d_tchunks, sizeof(RowChunk) * std::max<size_t>(t.size(), 1));
         if (e == cudaSuccess && !g.empty())
@@ -842,7 +911,8 @@ extern "C" sptrsv_status sptrsv_batch_plan_create(sptrsv_handle h, int32_t nmat,
             e = cudaMemcpy(p->d_tchunks, t.data(), sizeof(RowChunk) * t.size(), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) { sptrsv_plan_destroy(p); return from_cuda(e); }
     }
-    sptrsv_status st = rebuild_items(p);
+    sptrsv_status st = rebuild_items(p, 0);
+    if (st == SPTRSV_OK) st = rebuild_items(p, 1);
     if (st != SPTRSV_OK) { sptrsv_plan_destroy(p); return st; }
     *plan = p;
     return SPTRSV_OK;
@@ -852,23 +922,14 @@ extern "C" sptrsv_status sptrsv_batch_plan_set(sptrsv_plan p, const int32_t *row
                                                const int32_t *rhs_tile)
 {
     if (!p || !p->batched) return SPTRSV_EINVAL;
-    const int32_t nmat = (int32_t)p->h_mats.size();
-    for (int m = 0; m < nmat; ++m) {
-        if (rows_per_warp && rows_per_warp[m] != 0 && !valid_rpw(rows_per_warp[m])) return SPTRSV_EINVAL;
-        if (rhs_tile && rhs_tile[m] != 0 && !valid_tile(rhs_tile[m])) return SPTRSV_EINVAL;
-    }
-    const std::vector<int32_t> old_rpw = p->b_rpw, old_tile = p->b_tile;
-    for (int m = 0; m < nmat; ++m) {
-        if (rows_per_warp && rows_per_warp[m]) p->b_rpw[m] = rows_per_warp[m];
-        if (rhs_tile && rhs_tile[m]) p->b_tile[m] = rhs_tile[m];
-    }
-    sptrsv_status st = rebuild_items(p);
-    if (st == SPTRSV_ENOTSUP) {  // geometry does not fit: keep the previous one
-        p->b_rpw = old_rpw;
-        p->b_tile = old_tile;
-        if (rebuild_items(p) != SPTRSV_OK) return SPTRSV_ECUDA;
-    }
-    return st;
+    return set_geometry(p, 3, rows_per_warp, rhs_tile);
+}
+
+extern "C" sptrsv_status sptrsv_batch_plan_set_direction(sptrsv_plan p, int32_t direction,
+                                                         const int32_t *rows_per_warp, const int32_t *rhs_tile)
+{
+    if (!p || !p->batched || direction < 0 || direction > 2) return SPTRSV_EINVAL;
+    return set_geometry(p, direction == 0 ? 3 : direction, rows_per_warp, rhs_tile);
 }
 
 extern "C" sptrsv_status sptrsv_batch_offsets(sptrsv_plan p, int64_t *rhs_offset, int64_t *vals_offset)
@@ -883,23 +944,25 @@ namespace {
 sptrsv_status batch_solve_impl(sptrsv_plan p, const void *b, void *x, bool trans)
 {
     if (!p || !p->batched) return SPTRSV_EINVAL;
-    if (p->nitems == 0) return SPTRSV_OK;
+    const sptrsv_plan_st::Geom &G = p->geo[trans ? 1 : 0];
+    if (G.nitems == 0) return SPTRSV_OK;
     if (!b || !x) return SPTRSV_EINVAL;
     if (trans && !p->have_csc) return SPTRSV_ENOTSUP;
+    p->last_dir = trans ? 1 : 0;
     Waiter w{p->h->d_status, &p->d_ctl->abort_flag, p->spin};
     cudaError_t e = cudaSuccess;
     if (trans)
-        e = p->dtype == SPTRSV_F64 ? batch_csc_values<double>(p->d_mats, (int32_t)p->mats.size(), p->h->stream)
-                                   : batch_csc_values<float>(p->d_mats, (int32_t)p->mats.size(), p->h->stream);
+        e = p->dtype == SPTRSV_F64 ? batch_csc_values<double>(p->d_mats, p->d_ctiles, p->n_ctiles, p->h->stream)
+                                   : batch_csc_values<float>(p->d_mats, p->d_ctiles, p->n_ctiles, p->h->stream);
     if (e != cudaSuccess) return from_cuda(e);
     if (p->dtype == SPTRSV_F64)
-        e = batch_solve<double>(p->d_mats, p->d_items, p->nitems, p->d_order, (const double *)b, (double *)x,
-                                trans, p->d_ctl, w, p->batch_grid_sz, p->batch_smem, p->d_trace, p->withhold,
-                                p->h->stream);
+        e = batch_solve<double>(p->d_mats, G.d_items, G.nitems, G.d_order, (const double *)b, (double *)x,
+                                trans, p->d_ctl, w, G.grid, G.smem, p->d_trace, p->withhold,
+                                p->d_fchunks, p->n_fchunks, (double *)p->d_bt, p->h->stream);
     else
-        e = batch_solve<float>(p->d_mats, p->d_items, p->nitems, p->d_order, (const float *)b, (float *)x,
-                               trans, p->d_ctl, w, p->batch_grid_sz, p->batch_smem, p->d_trace, p->withhold,
-                                p->h->stream);
+        e = batch_solve<float>(p->d_mats, G.d_items, G.nitems, G.d_order, (const float *)b, (float *)x,
+                               trans, p->d_ctl, w, G.grid, G.smem, p->d_trace, p->withhold,
+                               p->d_fchunks, p->n_fchunks, (float *)p->d_bt, p->h->stream);
     return debug_sync(from_cuda(e), p->h->stream, "batch_solve");
 }
 }  // namespace
@@ -921,13 +984,14 @@ extern "C" sptrsv_status sptrsv_batch_trace(sptrsv_plan p, int64_t *trace)
     if (!p || !p->batched || !trace) return SPTRSV_EINVAL;
     const size_t nmat = p->mats.size();
     if (nmat == 0) return SPTRSV_OK;
-    std::vector<long long> t(3 * (size_t)p->nitems);
-    std::vector<BatchItem> items((size_t)p->nitems);
+    const sptrsv_plan_st::Geom &G = p->geo[p->last_dir];
+    std::vector<long long> t(3 * (size_t)G.nitems);
+    std::vector<BatchItem> items((size_t)G.nitems);
     cudaError_t e = cudaStreamSynchronize(p->h->stream);
-    if (e == cudaSuccess && p->nitems > 0)
+    if (e == cudaSuccess && G.nitems > 0)
         e = cudaMemcpy(t.data(), p->d_trace, sizeof(long long) * t.size(), cudaMemcpyDeviceToHost);
-    if (e == cudaSuccess && p->nitems > 0)
-        e = cudaMemcpy(items.data(), p->d_items, sizeof(BatchItem) * items.size(), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && G.nitems > 0)
+        e = cudaMemcpy(items.data(), G.d_items, sizeof(BatchItem) * items.size(), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return from_cuda(e);
     // per system: earliest start and latest end over its work items, and the
     // SM that started first
@@ -936,7 +1000,7 @@ extern "C" sptrsv_status sptrsv_batch_trace(sptrsv_plan p, int64_t *trace)
         trace[3 * m + 1] = 0;
         trace[3 * m + 2] = -1;
     }
-    for (int32_t it = 0; it < p->nitems; ++it) {
+    for (int32_t it = 0; it < G.nitems; ++it) {
         const int m = items[(size_t)it].mat;
         if (t[3 * (size_t)it] < trace[3 * m]) {
             trace[3 * m] = t[3 * (size_t)it];

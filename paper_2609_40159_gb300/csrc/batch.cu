@@ -26,21 +26,26 @@ __device__ __forceinline__ Sys<T> sys_of(const BatchMat &M)
 
 template <class T, int KT, bool TR>
 __device__ __forceinline__ bool run_one(const BatchMat &M, const BatchItem &I, unsigned char *raw,
-                                        const T *b, T *x, const Waiter &w, int withhold)
+                                        const T *b, const T *bt, T *x, const Waiter &w, int withhold)
 {
     const int ring = I.kc * I.rpw;
     BlockSmem<T, KT> sm = carve_block_smem<T, KT>(raw, ring, I.kc, I.nw);
     reset_block_smem<T, KT>(sm, ring, I.kc);
     __syncthreads();
+    Sys<T> A = sys_of<T>(M);
+    // a rewritten system's forward right-hand side b + T b was formed by the
+    // fold launch before this one (bt); the solve itself reads no T
+    const bool folded = !TR && bt != nullptr && M.tmask != nullptr;
+    if (folded) A.tmask = nullptr;
     Rhs<T> R;
-    R.b = b + M.rhs_off + I.r0;
+    R.b = (folded ? bt : b) + M.rhs_off + I.r0;
     R.x = x + M.rhs_off + I.r0;
     R.ld = M.k;
     R.k = I.kt;
     // test hook: a withheld row (counted over all systems) is never published
     const int64_t wh = (int64_t)withhold - M.row_off;
     const int local = (withhold >= 0 && wh >= 0 && wh < M.n) ? (int)wh : -1;
-    const bool ok = block_solve_any<T, KT, TR, false>(sys_of<T>(M), R, I.rpw, I.kc, I.P, I.nw, sm, w, local);
+    const bool ok = block_solve_any<T, KT, TR, false>(A, R, I.rpw, I.kc, I.P, I.nw, sm, w, local);
     __syncthreads();
     release_block_smem<T, KT>(sm, I.kc);
     return ok;
@@ -56,7 +61,7 @@ __device__ __forceinline__ unsigned sm_id()
 template <class T, bool TR>
 __global__ void __launch_bounds__(kBatchThreads, kBatchMinBlocks)
 k_batch(const BatchMat *__restrict__ mats, const BatchItem *__restrict__ items, int32_t nitems,
-        const int32_t *__restrict__ order, const T *b, T *x, PlanCtl *ctl, Waiter w,
+        const int32_t *__restrict__ order, const T *b, const T *bt, T *x, PlanCtl *ctl, Waiter w,
         long long *trace, int withhold)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -79,10 +84,10 @@ k_batch(const BatchMat *__restrict__ mats, const BatchItem *__restrict__ items, 
             trace[3 * it + 2] = (long long)sm_id();
         }
         switch (I.KT) {
-        case 1: run_one<T, 1, TR>(M, I, smraw, b, x, w, withhold); break;
-        case 2: run_one<T, 2, TR>(M, I, smraw, b, x, w, withhold); break;
-        case 4: run_one<T, 4, TR>(M, I, smraw, b, x, w, withhold); break;
-        default: run_one<T, 8, TR>(M, I, smraw, b, x, w, withhold); break;
+        case 1: run_one<T, 1, TR>(M, I, smraw, b, bt, x, w, withhold); break;
+        case 2: run_one<T, 2, TR>(M, I, smraw, b, bt, x, w, withhold); break;
+        case 4: run_one<T, 4, TR>(M, I, smraw, b, bt, x, w, withhold); break;
+        default: run_one<T, 8, TR>(M, I, smraw, b, bt, x, w, withhold); break;
         }
         __syncthreads();
         if (trace && threadIdx.x == 0) trace[3 * it + 1] = (long long)now_ns();
@@ -108,7 +113,9 @@ __device__ __forceinline__ int row_in_chunk(int s, int nrows, int p)
 // the chunk's nonzeros are contiguous in CSR order and are taken 32 at a
 // time, one per lane (coalesced column indices and gradient stores).
 // (Groups of up to 8 lanes per nonzero, reading g_b[i,:] and x[j,:] in
-// contiguous pieces, measured slower on the batched workload.)
+// contiguous pieces, measured slower on the batched workload; so did groups
+// of up to 32 lanes walking the chunk's rows: 8.4 ms instead of 3.0 ms for
+// T^T and the gradient, the extra instructions outweighing the coalescing.)
 template <class T>
 __global__ void k_batch_grad(const BatchMat *__restrict__ mats, const RowChunk *__restrict__ chunks,
                              int64_t nchunks, const T *__restrict__ gb, const T *__restrict__ x,
@@ -171,17 +178,57 @@ __global__ void k_batch_tt(const BatchMat *__restrict__ mats, const RowChunk *__
     }
 }
 
-// cv = v[tmap] for every system: blockIdx.y picks the system.
+// bt = b + T b for every row of the rewritten systems (the right-hand side
+// of L' x = b + T b, Section 2.2), one warp per 32-row chunk of those
+// systems.  The chunk's rows are contiguous in the packed layout, so the
+// warp copies its 32 k elements in order (coalesced) and adds the T terms
+// of the few rows that have a T row.  Formed once per forward batched solve
+// so that the solve kernel reads one right-hand side per row.
 template <class T>
-__global__ void k_batch_csc_values(const BatchMat *__restrict__ mats, int32_t nmat)
+__global__ void k_batch_tfold(const BatchMat *__restrict__ mats, const RowChunk *__restrict__ chunks,
+                              int64_t nchunks, const T *__restrict__ b, T *__restrict__ bt)
 {
-    for (int m = blockIdx.y; m < nmat; m += gridDim.y) {
-        const BatchMat &M = mats[m];
-        if (M.cv == nullptr) continue;
+    const int lane = threadIdx.x & 31;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t c = gw; c < nchunks; c += nw) {
+        const RowChunk ch = chunks[c];
+        const BatchMat &M = mats[ch.mat];
+        const int k = M.k;
+        const int nrows = min(32, M.n - ch.r0);
+        const unsigned word = ldro(M.tmask + (ch.r0 >> 5));
+        const T *bb = b + M.rhs_off;
+        const T *tv = (const T *)M.tv;
+        const int64_t e0 = (int64_t)ch.r0 * k;
+        const int64_t e1 = e0 + (int64_t)nrows * k;
+        for (int64_t t = e0 + lane; t < e1; t += 32) {
+            T v = bb[t];
+            const int i = (int)(t / k);
+            if ((word >> (i & 31)) & 1u) {
+                const int r = (int)(t - (int64_t)i * k);
+                for (int p = ldro(M.trp + i); p < ldro(M.trp + i + 1); ++p)
+                    v += ldro(tv + p) * bb[(int64_t)ldro(M.tci + p) * k + r];
+            }
+            bt[M.rhs_off + t] = v;
+        }
+    }
+}
+
+// cv = v[tmap] for every system, by tiles of kCscTile consecutive CSC
+// entries of one system taken in order (tile t by block t, t + grid, ...):
+// the blocks in flight work on a window of neighbouring tiles, whose source
+// values stay in L2 while they are gathered.
+template <class T>
+__global__ void k_batch_csc_values(const BatchMat *__restrict__ mats, const RowChunk *__restrict__ tiles,
+                                   int64_t ntiles)
+{
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const RowChunk tl = tiles[t];
+        const BatchMat &M = mats[tl.mat];
         const T *v = (const T *)M.v;
         T *cv = (T *)M.cv;
-        for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < M.nnz;
-             q += (int64_t)gridDim.x * blockDim.x)
+        const int64_t q1 = min((int64_t)tl.r0 + kCscTile, M.nnz);
+        for (int64_t q = (int64_t)tl.r0 + threadIdx.x; q < q1; q += blockDim.x)
             cv[q] = ldro(v + ldro(M.tmap + q));
     }
 }
@@ -214,16 +261,22 @@ template <class T>
 cudaError_t batch_solve(const BatchMat *mats, const BatchItem *items, int32_t nitems,
                         const int32_t *order, const T *b, T *x, bool trans, PlanCtl *ctl,
                         const Waiter &w, int grid, size_t smem, long long *trace, int withhold,
-                        cudaStream_t s)
+                        const RowChunk *fchunks, int64_t nfchunks, T *bt, cudaStream_t s)
 {
     cudaError_t e = launch_prologue<T>(ctl, s);
     if (e != cudaSuccess || nitems <= 0) return e;
+    const bool fold = !trans && bt != nullptr && nfchunks > 0;
+    if (fold) {
+        k_batch_tfold<T><<<elementwise_grid(nfchunks), 256, 0, s>>>(mats, fchunks, nfchunks, b, bt);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
     if (trans)
-        k_batch<T, true><<<grid, kBatchThreads, smem, s>>>(mats, items, nitems, order, b, x, ctl, w, trace,
-                                                            withhold);
+        k_batch<T, true><<<grid, kBatchThreads, smem, s>>>(mats, items, nitems, order, b, nullptr, x, ctl, w,
+                                                            trace, withhold);
     else
-        k_batch<T, false><<<grid, kBatchThreads, smem, s>>>(mats, items, nitems, order, b, x, ctl, w, trace,
-                                                             withhold);
+        k_batch<T, false><<<grid, kBatchThreads, smem, s>>>(mats, items, nitems, order, b, fold ? bt : nullptr,
+                                                             x, ctl, w, trace, withhold);
     return cudaGetLastError();
 }
 
@@ -247,11 +300,11 @@ cudaError_t batch_tt_apply(const BatchMat *mats, const RowChunk *tchunks, int64_
 }
 
 template <class T>
-cudaError_t batch_csc_values(const BatchMat *mats, int32_t nmat, cudaStream_t s)
+cudaError_t batch_csc_values(const BatchMat *mats, const RowChunk *tiles, int64_t ntiles, cudaStream_t s)
 {
-    if (nmat <= 0) return cudaSuccess;
-    const dim3 grid(64, (unsigned)std::min(nmat, 65535));
-    k_batch_csc_values<T><<<grid, 256, 0, s>>>(mats, nmat);
+    if (ntiles <= 0) return cudaSuccess;
+    const int grid = (int)std::min<int64_t>(ntiles, 152 * 8);
+    k_batch_csc_values<T><<<grid, 256, 0, s>>>(mats, tiles, ntiles);
     return cudaGetLastError();
 }
 
@@ -259,12 +312,12 @@ cudaError_t batch_csc_values(const BatchMat *mats, int32_t nmat, cudaStream_t s)
     template cudaError_t batch_solve<T>(const BatchMat *, const BatchItem *, int32_t,             \
                                         const int32_t *, const T *, T *, bool, PlanCtl *,        \
                                         const Waiter &, int, size_t, long long *, int,           \
-                                        cudaStream_t);                                           \
+                                        const RowChunk *, int64_t, T *, cudaStream_t);           \
     template cudaError_t batch_grad_vals<T>(const BatchMat *, const RowChunk *, int64_t,         \
                                             const T *, const T *, T *, cudaStream_t);            \
     template cudaError_t batch_tt_apply<T>(const BatchMat *, const RowChunk *, int64_t, int64_t, \
                                            const T *, T *, cudaStream_t);                        \
-    template cudaError_t batch_csc_values<T>(const BatchMat *, int32_t, cudaStream_t);
+    template cudaError_t batch_csc_values<T>(const BatchMat *, const RowChunk *, int64_t, cudaStream_t);
 SPT_INST(double)
 SPT_INST(float)
 #undef SPT_INST

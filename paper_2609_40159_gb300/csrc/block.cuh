@@ -23,6 +23,14 @@ template <class T, int KT> struct BlockSmem {
 };
 
 __device__ __forceinline__ void fence_cta() { asm volatile("fence.sc.cta;" ::: "memory"); }
+__device__ __forceinline__ void fence_acq_rel_cta() { asm volatile("fence.acq_rel.cta;" ::: "memory"); }
+
+__device__ __forceinline__ int ld_relaxed_cta_smem(const int *p)
+{
+    int v;
+    asm volatile("ld.relaxed.cta.shared.s32 %0, [%1];" : "=r"(v) : "r"(smem_addr(p)) : "memory");
+    return v;
+}
 
 // Solve one system with the whole thread block.  Rows are handled in
 // processing order by row groups of `rpw` rows taken from a shared ticket; a
@@ -279,20 +287,30 @@ __device__ bool block_solve_sweep(const Sys<T> &A, const Rhs<T> &R, int kc, int 
     const int wid = threadIdx.x >> 5;
     T *coef = sm.coef + (size_t)wid * 1024;
     const T *ring0 = const_cast<const T *>(sm.xr);
+    // row of position q in processing order (clamped into the system)
+    auto row_at = [&](int q) { return q < n ? (TR ? n - 1 - q : q) : (TR ? n - 1 : 0); };
+    // the row extents of a warp's next group are loaded one group ahead, so
+    // that a group's entries are one dependent load away when it starts
+    int a_nx = 0, e_nx = 0;
+    if (wid < nchunks) {
+        const int i0 = row_at(wid * 32 + lane);
+        a_nx = RV<T, TR>::beg(A, i0);
+        e_nx = RV<T, TR>::end(A, i0);
+    }
     // groups are dealt round-robin: warp w solves w, w + nwarps, ...
     for (int c = wid; c < nchunks; c += nwarps) {
         const int base = c * 32;
         const int pos = base + lane;
         const bool valid = pos < n;
-        const int i = valid ? (TR ? n - 1 - pos : pos) : (TR ? n - 1 : 0);
-        {
-            // pull a later group's entries towards L2
-            const int pn = min(pos + 32 * (nwarps + 1), n - 1);
-            prefetch_row<T, TR>(A, TR ? n - 1 - pn : pn);
-        }
+        const int i = row_at(pos);
         // ---- 1. independent of the solution
-        const int a = RV<T, TR>::beg(A, i);
-        const int e = RV<T, TR>::end(A, i);
+        const int a = a_nx;
+        const int e = e_nx;
+        if (c + nwarps < nchunks) {
+            const int inx = row_at(pos + 32 * nwarps);
+            a_nx = RV<T, TR>::beg(A, inx);
+            e_nx = RV<T, TR>::end(A, inx);
+        }
         const int safe = TR ? a - 1 : e;  // position of the diagonal entry
         const T rinv = valid ? T(1) / RV<T, TR>::diag(A, a, e) : T(0);
         T acc[KT], bv[KT];
@@ -331,14 +349,28 @@ __device__ bool block_solve_sweep(const Sys<T> &A, const Rhs<T> &R, int kc, int 
         // rare ones in group c-1 are left for the group's turn
         const bool longrow = valid && e - a > NP;
         bool tail_near = false, tail_ring = false;
-        for (int p = a + NP; longrow && p < e; ++p) {
-            const int pj = order_pos<TR>(n, RV<T, TR>::col(A, p));
-            if (pj >= base) {
-                dmask |= 1u << (pj - base);
-                coef[(pj - base) * 32 + lane] = RV<T, TR>::val(A, p) * rinv;
-            } else if (c - (pj >> 5) < kc) {
-                if (pj >= base - 32) tail_near = true;
-                else tail_ring = true;
+        for (int p0 = a + NP; longrow && p0 < e; p0 += 4) {
+            // four entries per round of loads (clamped to the row's last
+            // entry, which exists since p0 < e)
+            int pjs[4];
+            T vs[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int p = min(p0 + q, e - 1);
+                pjs[q] = order_pos<TR>(n, RV<T, TR>::col(A, p));
+                vs[q] = RV<T, TR>::val(A, p);
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (p0 + q >= e) break;
+                const int pj = pjs[q];
+                if (pj >= base) {
+                    dmask |= 1u << (pj - base);
+                    coef[(pj - base) * 32 + lane] = vs[q] * rinv;
+                } else if (c - (pj >> 5) < kc) {
+                    if (pj >= base - 32) tail_near = true;
+                    else tail_ring = true;
+                }
             }
         }
         const bool anylong = __any_sync(SPT_FULL_MASK, longrow);
@@ -374,6 +406,18 @@ __device__ bool block_solve_sweep(const Sys<T> &A, const Rhs<T> &R, int kc, int 
             }
         }
 
+        if constexpr (!TWO) {
+            // the ring pass after the turn is decided now: an entry in the
+            // ring keeps its value and becomes its slot's offset; any other
+            // entry reads slot 0 with weight 0.  Only loads and multiply-adds
+            // are left on the dependent chain.
+#pragma unroll
+            for (int u = 0; u < NP; ++u) {
+                const bool use = valid && a + u < e && jj[u] < base && c - (jj[u] >> 5) < kc;
+                vv[u] = use ? vv[u] : T(0);
+                jj[u] = use ? (jj[u] & rmask) * KT : 0;
+            }
+        }
         consume(rinv);
 #pragma unroll
         for (int r = 0; r < KT; ++r) consume(bv[r]);
@@ -397,16 +441,31 @@ __device__ bool block_solve_sweep(const Sys<T> &A, const Rhs<T> &R, int kc, int 
                         axpy_vec<T, KT>(RV<T, TR>::val(A, p), ring0 + (pj & rmask) * KT, acc);
                 }
             }
+            // relaxed polls, one acquire fence once the count is reached
+            // (PTX memory model: a relaxed read followed by fence.acq_rel is
+            // an acquire pattern), so that a poll costs one shared load; a
+            // warp two or more groups from its turn sleeps between polls, so
+            // that waiting warps leave the issue slots to the working ones
+            // (several work items share an SM)
             WaitClock clk;
-            while (ld_acquire_cta_smem(sm.ctr + 1) < c)
+            int done;
+            while ((done = ld_relaxed_cta_smem(sm.ctr + 1)) < c) {
+                if (c - done > 1) __nanosleep(200);
                 if (clk.expired(w)) { ok = false; break; }
+            }
+            fence_acq_rel_cta();
         }
         if (!__all_sync(SPT_FULL_MASK, ok)) return false;
-        const int lim = TWO ? base - 32 : base;  // ring entries below lim are applied now
+        if constexpr (TWO) {
+            const int lim = base - 32;  // ring entries below lim are applied now
 #pragma unroll
-        for (int u = 0; u < NP; ++u) {
-            const bool use = valid && a + u < e && jj[u] < lim && c - (jj[u] >> 5) < kc;
-            axpy_vec<T, KT>(use ? vv[u] : T(0), ring0 + (use ? (jj[u] & rmask) * KT : 0), acc);
+            for (int u = 0; u < NP; ++u) {
+                const bool use = valid && a + u < e && jj[u] < lim && c - (jj[u] >> 5) < kc;
+                axpy_vec<T, KT>(use ? vv[u] : T(0), ring0 + (use ? (jj[u] & rmask) * KT : 0), acc);
+            }
+        } else {
+#pragma unroll
+            for (int u = 0; u < NP; ++u) axpy_vec<T, KT>(vv[u], ring0 + jj[u], acc);
         }
         if constexpr (TWO) {
             if (__any_sync(SPT_FULL_MASK, tail_ring)) {

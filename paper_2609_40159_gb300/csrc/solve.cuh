@@ -150,27 +150,34 @@ struct BatchItem {
     int32_t nw;       // active warps of the thread block
 };
 
-// One persistent launch: thread blocks take work items in `order` from the
-// control block's ticket and solve each with the block algorithm; trace
-// receives (start ns, end ns, SM) per item.
-template <class T>
-cudaError_t batch_solve(const BatchMat *mats, const BatchItem *items, int32_t nitems,
-                        const int32_t *order, const T *b, T *x, bool trans, PlanCtl *ctl,
-                        const Waiter &w, int grid, size_t smem, long long *trace, int withhold,
-                        cudaStream_t s);
-// cv[q] = v[tmap[q]]: the values of L in CSC order, so that the transpose
-// solves read them without the indirection (refreshed before every
-// transpose solve: the plan does not assume that L's values stay fixed).
-template <class T>
-cudaError_t csc_values(const int32_t *tmap, const T *v, T *cv, int64_t nnz, cudaStream_t s);
-template <class T>
-cudaError_t batch_csc_values(const BatchMat *mats, int32_t nmat, cudaStream_t s);
-
 // 32 consecutive rows (fewer at a system's end) of one system of a batch.
 struct RowChunk {
     int32_t mat;
     int32_t r0;  // a multiple of 32
 };
+
+// One persistent launch: thread blocks take work items in `order` from the
+// control block's ticket and solve each with the block algorithm; trace
+// receives (start ns, end ns, SM) per item.  Forward solves of batches with
+// rewritten systems first form bt = b + T b on every 32-row chunk of those
+// systems (fchunks, nfchunks; bt: plan-owned, packed like b) and the solve
+// reads bt for them.
+template <class T>
+cudaError_t batch_solve(const BatchMat *mats, const BatchItem *items, int32_t nitems,
+                        const int32_t *order, const T *b, T *x, bool trans, PlanCtl *ctl,
+                        const Waiter &w, int grid, size_t smem, long long *trace, int withhold,
+                        const RowChunk *fchunks, int64_t nfchunks, T *bt, cudaStream_t s);
+// cv[q] = v[tmap[q]]: the values of L in CSC order, so that the transpose
+// solves read them without the indirection (refreshed before every
+// transpose solve: the plan does not assume that L's values stay fixed).
+template <class T>
+cudaError_t csc_values(const int32_t *tmap, const T *v, T *cv, int64_t nnz, cudaStream_t s);
+// Tiles: (system, first CSC entry) of kCscTile entries each, every system
+// with a CSC, in system order.
+constexpr int kCscTile = 4096;
+template <class T>
+cudaError_t batch_csc_values(const BatchMat *mats, const RowChunk *tiles, int64_t ntiles, cudaStream_t s);
+
 // Value gradients of all matrices; chunks covers every row of every system
 // (device table of nchunks entries).
 template <class T>

@@ -20,7 +20,8 @@ class _FakeBatch:
         self.tile = [8] * len(mats)
         self.calls = 0
 
-    def set_geometry(self, rows_per_warp=None, rhs_tile=None):
+    def set_geometry(self, rows_per_warp=None, rhs_tile=None, direction="both"):
+        self.direction = direction
         if rows_per_warp is not None:
             self.rpw = [r if r else self.rpw[m] for m, r in enumerate(rows_per_warp)]
         if rhs_tile is not None:
@@ -29,6 +30,8 @@ class _FakeBatch:
     def solve(self, b, out=None):
         self.calls += 1
         return out
+
+    solve_transpose = solve
 
     def model_ms(self):
         # per system: chain cost grows with the tile, items = ceil(k / tile);
@@ -68,3 +71,27 @@ def test_batch_classes_bucket_row_length_and_rhs():
     fake = _FakeBatch([_Mat(100, 1000), _Mat(200, 2000), _Mat(100, 100)], [1, 1, 30])
     labels = autotune.batch_classes(fake)
     assert labels[0] == labels[1] and labels[0] != labels[2]
+
+
+def test_tune_batch_direction_sets_that_direction_only(monkeypatch):
+    """The transpose solve is tuned on its own timing and its geometry is set
+    for the transpose direction only."""
+    mats = [_Mat(1000 * (m + 1), 10_000 * (m + 1)) for m in range(6)]
+    fake = _FakeBatch(mats, [1, 4, 8, 16, 2, 32])
+    timed = []
+
+    def tc(fn, reps=3):
+        timed.append(fn)
+        fn()
+        return fake.model_ms()
+
+    monkeypatch.setattr(autotune, "time_call", tc)
+    calls = []
+    fake.solve_transpose = lambda b, out=None: calls.append("T") or out
+    fake.solve = lambda b, out=None: calls.append("F") or out
+    res = autotune.tune_batch(fake, torch.zeros(4), reps=1, direction="transpose")
+    assert res["direction"] == "transpose" and fake.direction == "transpose"
+    assert calls and set(calls) == {"T"}
+    import pytest
+    with pytest.raises(ValueError):
+        autotune.tune_batch(fake, torch.zeros(4), direction="sideways")
