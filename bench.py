@@ -51,7 +51,32 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip baseline/single/cpu legs")
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--ncu", action="store_true", help="minimal run for a profiler launch list")
+    ap.add_argument("--profile-single", type=int, default=0, metavar="N",
+                    help="profiling run only: level analysis, level-persistent and sync-free solves "
+                         "(FP64, 1 RHS) of the N x N 2D Laplacian, 3 times each; prints timings")
     return ap.parse_args()
+
+
+def profile_single(N):
+    """A small single-system case for a profiler: the kernels of the level
+    analysis, the level-persistent and the sync-free solve on the N x N 2D
+    Laplacian (2N-1 levels), each run 3 times after one warm-up."""
+    import torch
+    import paper_2609_40159_gb300 as P
+    from paper_2609_40159_gb300 import autotune
+    A = P.Matrix.from_host(S.lap2d(N))
+    b = torch.as_tensor(S.rhs(A.n, 1, seed=1)).cuda()
+    x = torch.empty_like(b)
+    out = {"n": A.n, "levels": 2 * N - 1}
+    out["analyze_ms"] = autotune.time_call(lambda: P.analyze(A), reps=3, warmup=1)
+    plan = P.Plan(A)
+    for mode in ("level", "syncfree"):
+        plan.set(mode, 32, 1)
+        ms = autotune.time_call(lambda: plan.solve(b, out=x), reps=3, warmup=1)
+        out[mode] = {"ms": ms, "us_per_level": 1e3 * ms / (2 * N - 1)}
+    if P.handle().status() != 0:
+        raise RuntimeError("device status after the profiling run")
+    print(json.dumps(out), flush=True)
 
 
 # ------------------------------------------------------------------ bytes
@@ -233,6 +258,9 @@ def build_batch(P, items, dev):
 
 def main():
     args = parse()
+    if args.profile_single:
+        profile_single(args.profile_single)
+        return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
