@@ -147,13 +147,19 @@ sptrsv_status sptrsv_analyze(sptrsv_handle handle, const sptrsv_csr *L, int32_t 
 /* The same analysis after a change confined to rows >= first_row (e.g. a
  * rewrite whose rewritten rows are all >= first_row, Section 2.2: rewriting
  * row i changes row i only, so every earlier row keeps its level).  lev is
- * in/out: on entry lev[0 .. first_row) must hold the levels of those rows
- * (e.g. from sptrsv_analyze of the matrix before the change); the rows from
- * 32 * floor(first_row / 32) on are recomputed, then perm, level_ptr,
- * level_cost, *nlevels and stats as sptrsv_analyze.  first_row outside
- * [0, n] is SPTRSV_EINVAL; first_row = 0 is sptrsv_analyze.  The results
- * equal sptrsv_analyze's when the entry levels are right; wrong entry levels
- * are not detected.  Synchronises.                                          */
+ * in/out: on entry it must hold the levels of the matrix BEFORE the change
+ * (e.g. from sptrsv_analyze of that matrix); only levels that the change
+ * actually moves are recomputed: rounds over the rows >= first_row, the
+ * first recomputing all of them, each later one only the rows with a
+ * predecessor changed in the round before, until a round changes nothing
+ * (one launch, the environment step of the paper's Section 4.1: a rewrite
+ * usually moves one row).  A change that propagates through more than 64
+ * rounds (a level that empties renumbers every later level) is finished by
+ * the full sync-free pass from its first unsettled row.  Then perm,
+ * level_ptr, level_cost, *nlevels and stats as sptrsv_analyze.  first_row
+ * outside [0, n] is SPTRSV_EINVAL; first_row = 0 is sptrsv_analyze.  The
+ * results equal sptrsv_analyze's when the entry levels are right; wrong
+ * entry levels are not detected.  Synchronises.                             */
 sptrsv_status sptrsv_analyze_incremental(sptrsv_handle handle, const sptrsv_csr *L, int32_t first_row,
                                          int32_t *lev, int32_t *perm, int32_t *level_ptr,
                                          int64_t *level_cost, int32_t *nlevels, double stats[6]);

@@ -14,6 +14,7 @@
 //                to double once), so that they are reproducible bit for bit.
 //   partition -- perm = rows sorted by (level, row): stable radix sort by level.
 #include <climits>
+#include <vector>
 
 #include "common.cuh"
 #include "internal.h"
@@ -182,6 +183,84 @@ k_levels(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, int32_t
 }
 
 __global__ void k_set_counter(unsigned long long *counter, unsigned long long v) { *counter = v; }
+
+// Grid-wide barrier of a cooperative launch (every block resident): block
+// leaders count arrivals; the last one resets the count and advances the
+// generation (release), the others wait for the generation to move
+// (acquire).  Bounded; false on timeout or abort.
+__device__ bool grid_sync(unsigned *arrive, unsigned *gen, unsigned nblocks, const Waiter &w)
+{
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        s_ok = 1;
+        const unsigned g = ld_acquire(gen);
+        __threadfence();
+        if (atomicAdd(arrive, 1u) == nblocks - 1) {
+            *arrive = 0u;
+            st_release(gen, g + 1u);
+        } else {
+            WaitClock clk;
+            while (ld_acquire(gen) == g)
+                if (clk.expired(w)) { s_ok = 0; break; }
+        }
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+constexpr int kUpdThreads = 256;
+
+// Levels after a change confined to rows >= first_row, as a fixpoint of
+// lev[i] = 1 + max over predecessors (0 without), starting from the levels
+// before the change (valid for every row < first_row).  Round 1 recomputes
+// every row >= first_row from the current values; round r > 1 only the rows
+// with a predecessor whose level changed in round r - 1 or later
+// (stamp[j] = last round in which lev[j] changed, 0 = never).  A round that
+// changes nothing ends the loop: then every row satisfies the recurrence,
+// whose solution on a DAG is unique.  cnt[r] / minrow[r] receive the number
+// of rows changed in round r and the smallest of them; after max_rounds
+// rounds with changes the host finishes from minrow[max_rounds] with the
+// sync-free pass (every row below it is final).  One launch with grid-wide
+// barriers between rounds (cooperative launch: all blocks resident).
+__global__ void __launch_bounds__(kUpdThreads)
+k_levels_update(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, int32_t n, int32_t first_row,
+                int32_t *lev, int32_t *stamp, int32_t *cnt, int32_t *minrow, unsigned *bar, int max_rounds,
+                Waiter w, int32_t withhold)
+{
+    __shared__ int s_cnt, s_min;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nth = (int64_t)gridDim.x * blockDim.x;
+    for (int r = 1; r <= max_rounds; ++r) {
+        if (threadIdx.x == 0) { s_cnt = 0; s_min = INT_MAX; }
+        __syncthreads();
+        int my_cnt = 0, my_min = INT_MAX;
+        for (int64_t ii = first_row + tid; ii < n; ii += nth) {
+            const int i = (int)ii;
+            const int a = ldro(rp + i), e = ldro(rp + i + 1) - 1;
+            bool cand = r == 1;
+            for (int p = a; p < e && !cand; ++p) cand = ld_relaxed(stamp + ldro(ci + p)) >= r - 1;
+            if (!cand) continue;
+            int m = -1;
+            for (int p = a; p < e; ++p) m = max(m, ld_relaxed(lev + ldro(ci + p)));
+            if (m + 1 != ld_relaxed(lev + i)) {
+                st_relaxed(lev + i, m + 1);
+                st_relaxed(stamp + i, r);
+                ++my_cnt;
+                my_min = min(my_min, i);
+            }
+        }
+        my_cnt = __reduce_add_sync(SPT_FULL_MASK, (unsigned)my_cnt);
+        my_min = __reduce_min_sync(SPT_FULL_MASK, my_min);
+        if ((threadIdx.x & 31) == 0 && my_cnt) { atomicAdd(&s_cnt, my_cnt); atomicMin(&s_min, my_min); }
+        __syncthreads();
+        if (threadIdx.x == 0 && s_cnt) { atomicAdd(cnt + r, s_cnt); atomicMin(minrow + r, s_min); }
+        // test hook: the first block never arrives at the first barrier
+        if (withhold >= 0 && blockIdx.x == 0) return;
+        if (!grid_sync(bar, bar + 1, gridDim.x, w)) return;
+        if (ld_relaxed(cnt + r) == 0) return;  // uniform: read after the barrier
+    }
+}
 
 __global__ void k_count_long(const int32_t *rp, int32_t n, int32_t min_offdiag, unsigned long long *out)
 {
@@ -383,6 +462,51 @@ cudaError_t launch_levels(const sptrsv_csr &L, int32_t *lev, const Ctl &ctl, lon
     Waiter w{ctl.status, ctl.abort_flag, limit_ns};
     k_levels<<<(int)blocks, kLevThreads, 0, s>>>(L.row_ptr, L.col_idx, L.n, lev, ctl.counters, w, withhold);
     return cudaGetLastError();
+}
+
+cudaError_t launch_levels_update(const sptrsv_csr &L, int32_t first_row, int32_t *lev, const Ctl &ctl,
+                                 long long limit_ns, const DeviceInfo &di, cudaStream_t s, int max_rounds,
+                                 int32_t withhold, bool *converged, int32_t *restart_row)
+{
+    *converged = true;
+    *restart_row = L.n;
+    const int64_t rows = (int64_t)L.n - first_row;
+    if (rows <= 0) return cudaSuccess;
+    // scratch: stamp[n], cnt[R+1], minrow[R+1], barrier {count, generation}
+    const size_t nstamp = (size_t)L.n, nr = (size_t)max_rounds + 1;
+    int32_t *buf = nullptr;
+    cudaError_t e = cudaMallocAsync(&buf, sizeof(int32_t) * (nstamp + 2 * nr + 2), s);
+    if (e != cudaSuccess) return e;
+    int32_t *stamp = buf, *cnt = buf + nstamp, *minrow = cnt + nr;
+    unsigned *bar = reinterpret_cast<unsigned *>(minrow + nr);
+    e = cudaMemsetAsync(stamp, 0, sizeof(int32_t) * (nstamp + nr), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(minrow, 0x7f, sizeof(int32_t) * nr, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), s);
+    int per_sm = 0;
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_levels_update, kUpdThreads, 0);
+    if (e == cudaSuccess) {
+        int64_t grid = (int64_t)std::max(per_sm, 1) * di.num_sms;
+        grid = std::min<int64_t>(grid, (rows + kUpdThreads - 1) / kUpdThreads);
+        Waiter w{ctl.status, ctl.abort_flag, limit_ns};
+        int32_t n = L.n;
+        const int32_t *rp = L.row_ptr, *ci = L.col_idx;
+        void *args[] = {(void *)&rp, (void *)&ci, (void *)&n, (void *)&first_row, (void *)&lev, (void *)&stamp,
+                        (void *)&cnt, (void *)&minrow, (void *)&bar, (void *)&max_rounds, (void *)&w,
+                        (void *)&withhold};
+        e = cudaLaunchCooperativeKernel((const void *)k_levels_update, dim3((unsigned)grid), dim3(kUpdThreads),
+                                        args, 0, s);
+    }
+    std::vector<int32_t> hc(nr), hm(nr);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hc.data(), cnt, sizeof(int32_t) * nr, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hm.data(), minrow, sizeof(int32_t) * nr, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFreeAsync(buf, s);
+    if (e != cudaSuccess) return e;
+    bool done = false;
+    for (int r = 1; r <= max_rounds && !done; ++r) done = hc[r] == 0;
+    *converged = done;
+    if (!done) *restart_row = hm[max_rounds];
+    return cudaSuccess;
 }
 
 cudaError_t launch_count_long(const int32_t *rp, int32_t n, int32_t min_offdiag,

@@ -23,6 +23,7 @@ struct Range {
     ~Range() { nvtxRangePop(); }
 };
 constexpr long long kDefaultWaitNs = 10ll * 1000 * 1000 * 1000;  // 10 s
+constexpr int kUpdateRounds = 64;  // fixpoint rounds of an incremental analysis before the full pass
 
 bool debug_mode()
 {
@@ -264,12 +265,29 @@ sptrsv_status levels_impl(sptrsv_handle h, const sptrsv_csr &L, int32_t *lev, in
     sptrsv_status st = validate_impl(h, L, nullptr);
     if (st != SPTRSV_OK || L.n == 0) return st;
     cudaStream_t s = h->stream;
-    const int64_t c0 = first_row / 32;
-    cudaError_t e = cudaMemsetAsync(lev + 32 * c0, 0xFF, sizeof(int32_t) * (size_t)(L.n - 32 * c0), s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(&h->d_ctl->abort_flag, 0, sizeof(int), s);
+    cudaError_t e = cudaMemsetAsync(&h->d_ctl->abort_flag, 0, sizeof(int), s);
     Ctl ctl{h->d_status, &h->d_ctl->abort_flag, &h->d_ctl->ticket};
     if (h->dbg_withhold >= 0 && h->dbg_wait_ns > 0) spin = h->dbg_wait_ns;
-    if (e == cudaSuccess) e = launch_levels(L, lev, ctl, spin, h->di, s, c0, h->dbg_withhold);
+    int32_t restart = 0;  // rows from here on are (re)computed by the sync-free pass
+    if (first_row > 0 && e == cudaSuccess) {
+        // after a change confined to rows >= first_row: fixpoint rounds from
+        // the previous levels; a change that propagates through more than
+        // kUpdateRounds rounds (a level collapse renumbers every later level)
+        // is finished by the sync-free pass from the first unsettled row
+        bool converged = false;
+        e = launch_levels_update(L, first_row, lev, ctl, spin, h->di, s, kUpdateRounds, h->dbg_withhold,
+                                 &converged, &restart);
+        int hab0 = 0;
+        if (e == cudaSuccess) e = cudaMemcpy(&hab0, &h->d_ctl->abort_flag, sizeof(int), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return from_cuda(e);
+        if (hab0) return SPTRSV_ETIMEOUT;
+        if (converged) restart = L.n;
+    }
+    const int64_t c0 = restart / 32;
+    if (e == cudaSuccess && 32 * c0 < L.n) {
+        e = cudaMemsetAsync(lev + 32 * c0, 0xFF, sizeof(int32_t) * (size_t)(L.n - 32 * c0), s);
+        if (e == cudaSuccess) e = launch_levels(L, lev, ctl, spin, h->di, s, c0, h->dbg_withhold);
+    }
     int32_t *dmax = reinterpret_cast<int32_t *>(h->d_scratch + 1);
     if (e == cudaSuccess) e = launch_max(lev, L.n, dmax, s);
     int32_t hm = -1;

@@ -49,6 +49,13 @@ cudaError_t launch_validate(const sptrsv_csr &L, long long *out_dev, cudaStream_
 cudaError_t launch_levels(const sptrsv_csr &L, int32_t *lev, const Ctl &ctl,
                           long long limit_ns, const DeviceInfo &di, cudaStream_t s,
                           int64_t first_chunk = 0, int32_t withhold = -1);
+// Levels after a change confined to rows >= first_row (lev: the levels before
+// the change): fixpoint rounds in one cooperative launch (synchronises).
+// *converged: the rounds reached the fixpoint; otherwise every row below
+// *restart_row is final and the rest must be recomputed (launch_levels).
+cudaError_t launch_levels_update(const sptrsv_csr &L, int32_t first_row, int32_t *lev, const Ctl &ctl,
+                                 long long limit_ns, const DeviceInfo &di, cudaStream_t s, int max_rounds,
+                                 int32_t withhold, bool *converged, int32_t *restart_row);
 // Thin flags, fewest-dependency row per level, and (thin count, max rows in
 // a thin level, max cost of a thin level) -> out_dev[0..2].
 cudaError_t launch_level_summary(const int32_t *rp, const int32_t *perm, const int32_t *level_ptr,

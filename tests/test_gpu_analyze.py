@@ -155,6 +155,88 @@ def test_incremental_after_rewrite(gen):
     assert torch.equal(same.lev, full.lev)
 
 
+def _check_same_analysis(inc, full, ref):
+    for f in ("lev", "perm", "level_ptr", "cost"):
+        assert torch.equal(getattr(full, f), getattr(inc, f)), f
+    assert inc.nlevels == full.nlevels and np.array_equal(inc.stats, full.stats)
+    assert np.array_equal(inc.lev.cpu().numpy(), ref["lev"])
+    assert np.array_equal(inc.perm.cpu().numpy(), ref["perm"])
+    assert np.array_equal(inc.stats, ref["stats"])
+
+
+@pytest.mark.parametrize("gen", ["lap2d_256", "band", "powerlaw"])
+def test_incremental_single_row_moves(gen):
+    """The environment's step: one more row rewritten at a time (the rewrite
+    list grows by one row per move; every listed row is rewritten from the
+    original rows, so consecutive systems differ in that row only).  After
+    every move the incremental analysis from that row, seeded with the
+    previous levels, equals the full analysis and the oracle bit for bit."""
+    import paper_2609_40159_gb300 as P
+    A_h = {"band": lambda: S.band_random(20_000, 64, 2, 10, seed=21),
+           "lap2d_256": lambda: S.lap2d(256),
+           "powerlaw": lambda: S.powerlaw(100_000, seed=22)}[gen]()
+    A = P.Matrix.from_host(A_h)
+    an0 = P.analyze(A)
+    lev0 = an0.lev.cpu().numpy()
+    rng = np.random.default_rng(5)
+    cand = np.flatnonzero(lev0 >= 2)
+    rows, tgs = [], []
+    prev = an0
+    for move in range(12):
+        i = int(rng.choice(cand))
+        rows.append(i)
+        tgs.append(int(rng.integers(max(0, lev0[i] - 6), lev0[i])))
+        Lp, _ = P.rewrite(A, an0.lev, rows, tgs)
+        inc = P.analyze(Lp, prev_lev=prev.lev, first_row=i)
+        full = P.analyze(Lp)
+        ref = oracle.analyze(oracle.rewrite(A_h, lev0, rows, tgs)[0])
+        _check_same_analysis(inc, full, ref)
+        prev = inc
+
+
+def test_incremental_level_collapse_falls_back():
+    """A move that empties a level renumbers every later level: in a chain
+    (one row per level) rewriting row 1500 two levels up moves every row after
+    it, a propagation longer than the fixpoint's round limit, finished by the
+    full pass from the first unsettled row; still equal to the full analysis
+    and the oracle."""
+    import paper_2609_40159_gb300 as P
+    A_h = S.chain(3000, seed=4)
+    A = P.Matrix.from_host(A_h)
+    an0 = P.analyze(A)
+    Lp, _ = P.rewrite(A, an0.lev, [1500], [1498])
+    inc = P.analyze(Lp, prev_lev=an0.lev, first_row=1500)
+    full = P.analyze(Lp)
+    assert full.nlevels == 2998  # row 1500 lands on level 1498; every later row moves up two levels
+    _check_same_analysis(inc, full, oracle.analyze(oracle.rewrite(A_h, an0.lev.cpu().numpy(), [1500], [1498])[0]))
+
+
+def test_incremental_bounded_wait_reports_timeout():
+    """The grid-wide barrier of the incremental analysis is bounded too: with
+    the analysis test hook one block never arrives, the others give up after
+    the hook's limit, the call returns SPTRSV_ETIMEOUT and the next one is
+    right."""
+    import paper_2609_40159_gb300 as P
+    A_h = S.band_random(300_000, 64, 2, 10, seed=23)
+    A = P.Matrix.from_host(A_h)
+    an0 = P.analyze(A)
+    lev0 = an0.lev.cpu().numpy()
+    i = int(np.flatnonzero(lev0 >= 3)[1000])
+    Lp, _ = P.rewrite(A, an0.lev, [i], [int(lev0[i]) - 2])
+    h = P.handle()
+    h.withhold_level(0, wait_limit_us=20_000)
+    try:
+        with pytest.raises(P.SpTRSVError) as e:
+            P.analyze(Lp, prev_lev=an0.lev, first_row=i)
+        assert e.value.status == P._lib.SPTRSV_ETIMEOUT
+        assert h.status() == P._lib.SPTRSV_ETIMEOUT
+    finally:
+        h.withhold_level(-1)
+    inc = P.analyze(Lp, prev_lev=an0.lev, first_row=i)
+    _check_same_analysis(inc, P.analyze(Lp), oracle.analyze(oracle.rewrite(A_h, lev0, [i], [int(lev0[i]) - 2])[0]))
+    assert h.status() == 0
+
+
 def test_incremental_bad_first_row():
     import ctypes as C
     import paper_2609_40159_gb300 as P
