@@ -11,8 +11,10 @@ from ._lib import SpTRSVError
 from .api import (Analysis, BatchPlan, Handle, Matrix, Plan, UpperPlan, analyze, handle, level_summary, rewrite,
                   transpose, validate)
 from .autograd import BatchSpTRSVFunction, SpTRSVFunction, batch_solve, solve
+from .env import EnvConfig, RewriteEnv
 
 __all__ = [
     "_lib", "SpTRSVError", "Analysis", "BatchPlan", "Handle", "Matrix", "Plan", "analyze", "handle", "rewrite",
     "validate", "level_summary", "transpose", "UpperPlan", "SpTRSVFunction", "BatchSpTRSVFunction", "solve", "batch_solve",
+    "EnvConfig", "RewriteEnv",
 ]
