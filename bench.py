@@ -569,9 +569,11 @@ def _host_ms(fn, reps=3):
     return best
 
 
-def _single_config(P, A_h, dev, k, autotune):
+def _single_config(P, A_h, dev, k, autotune, modes_run=("level_launch", "level", "syncfree"), modes=None):
     """Analysis, rewrite (narrowest-level 1 %, chunks of 8 levels) and the
-    forward solve in every mode on the original and the rewritten DAG."""
+    forward solve in every mode (or the given ones) on the original and the
+    rewritten DAG."""
+    modes_run = modes if modes is not None else modes_run
     import torch
     A = P.Matrix.from_host(A_h, device=dev)
     an = P.analyze(A)
@@ -591,7 +593,7 @@ def _single_config(P, A_h, dev, k, autotune):
     for name, (M, TT) in {"orig": (A, None), "rewritten": (Lp, T)}.items():
         p = P.Plan(M, TT)
         nb = bytes_fwd(M.n, M.nnz, k, 8, M.n if TT is not None else 0, TT.nnz if TT is not None else 0)
-        for mode in ("level_launch", "level", "syncfree"):
+        for mode in modes_run:
             p.set(mode, 0, 0)
             ms = autotune.time_call(lambda: p.solve(b, out=x), reps=3, warmup=1)
             modes[f"{name}:{mode}"] = {"us": 1e3 * ms, "gbs": nb / (ms * 1e-3) / 1e9}
@@ -628,6 +630,104 @@ def _diff_config(P, A_h, dev, k, autotune):
     return res
 
 
+def _time_cold(fn, reps, flush):
+    """Median ms of fn() with L2 flushed before every call (a write of
+    `flush`, twice the L2 size, between the calls; CUDA events)."""
+    import torch
+    fn()
+    ts = []
+    for _ in range(reps):
+        flush.add_(1.0)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        b.synchronize()
+        ts.append(a.elapsed_time(b))
+    return float(np.median(ts))
+
+
+def _lap2d_config(P, dev, dt, autotune):
+    """2D Laplacian 1024^2 in one value type: level analysis, rewrite of the
+    narrowest 1 % of levels, every solve mode on the original and the
+    rewritten DAG, warm (L2-resident: 59 MB FP64 / 38 MB FP32 fit in the
+    L2) and cold (L2 flushed before every solve)."""
+    import torch
+    A_h = S.lap2d(1024, dtype=dt)
+    A = P.Matrix.from_host(A_h, device=dev)
+    an = P.analyze(A)
+    rows, tg = S.narrowest_levels_list(an.nlevels, an.level_ptr.cpu().numpy(), an.perm.cpu().numpy(), 0.01, 8)
+    Lp, T = P.rewrite(A, an.lev, rows, tg)
+    an2 = P.analyze(Lp)
+    wv = np.dtype(dt).itemsize
+    b = torch.as_tensor(S.rhs(A_h.n, 1, seed=1, dtype=dt)).to(dev)
+    x = torch.empty_like(b)
+    l2 = getattr(torch.cuda.get_device_properties(dev), "L2_cache_size", 128 << 20) or (128 << 20)
+    flush = torch.empty(2 * l2 // 4, dtype=torch.float32, device=dev)
+    res = {"levels_orig": an.nlevels, "levels_rewritten": an2.nlevels,
+           "cv_cost_orig": float(an.stats[3]), "cv_cost_rewritten": float(an2.stats[3]),
+           "rows_rewritten": int(len(rows)), "nnz_T": int(T.nnz), "nnz_Lp": int(Lp.nnz),
+           "l2_flush_bytes": int(flush.numel() * 4)}
+    modes = {}
+    for name, (M, TT) in {"orig": (A, None), "rewritten": (Lp, T)}.items():
+        p = P.Plan(M, TT)
+        nb = bytes_fwd(M.n, M.nnz, 1, wv, M.n if TT is not None else 0, TT.nnz if TT is not None else 0)
+        for mode in ("level_launch", "level", "syncfree", "block"):
+            p.set(mode, 32, 1)
+            ms = autotune.time_call(lambda: p.solve(b, out=x), reps=5, warmup=2)
+            msc = _time_cold(lambda: p.solve(b, out=x), 3, flush)
+            modes[f"{name}:{mode}"] = {"us": 1e3 * ms, "us_cold_l2": 1e3 * msc, "gbs": nb / (ms * 1e-3) / 1e9,
+                                       "us_per_level": 1e3 * ms / (an.nlevels if TT is None else an2.nlevels)}
+    res["fwd"] = modes
+    # analysis, rewrite and the incremental re-analysis (host-timed, each call synchronises)
+    an_ms = _host_ms(lambda: P.analyze(A))
+    rw_ms = _host_ms(lambda: P.rewrite(A, an.lev, rows, tg))
+    inc_ms = _host_ms(lambda: P.analyze(Lp, prev_lev=an.lev, first_row=int(np.min(rows))))
+    res["preprocess_ms"] = {"analyze": an_ms, "rewrite_1pct": rw_ms, "analyze_incremental_after_rewrite": inc_ms,
+                            "analyze_gbs": (A.nnz * (wv + 4) + (A.n + 1) * 4 + A.n * 4) / (an_ms * 1e-3) / 1e9}
+    return res
+
+
+def _env_config(P, A_h, dev, moves=30):
+    """The paper's environment step on the GPU kernels (RewriteEnv): a
+    scripted policy (highest source affinity, then fewest rows, then lowest
+    level) makes `moves` moves; host-timed per move (every move rewrites the
+    list, re-analyses incrementally from the moved row and reads the level
+    summary back), then one move's calls timed apart."""
+    import torch
+    env = P.RewriteEnv(P.Matrix.from_host(A_h, device=dev))
+    L0 = env.nlevels
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    valid = collapses = done = 0
+    per_move = []
+    for _ in range(moves):
+        if env.done():
+            break
+        tm = time.perf_counter()
+        mask = env.valid_actions()
+        cands = np.flatnonzero(mask)
+        ls = int(min(cands, key=lambda l: (-env.src_aff[l], env.level_rows[l], l)))
+        _, info = env.step(ls)
+        per_move.append(1e3 * (time.perf_counter() - tm))
+        valid += info["valid"]
+        collapses += bool(info["valid"] and info["collapsed"] > 0)
+        done += 1
+    dt = time.perf_counter() - t0
+    row = env.rows[-1] if env.rows else 0
+    prev_lev = env.an.lev.clone()
+    rw = _host_ms(lambda: P.rewrite(env.A, env.an0.lev, env.rows, env.targets))
+    inc = _host_ms(lambda: P.analyze(env.Lp, prev_lev=prev_lev, first_row=row))
+    summ = _host_ms(lambda: P.level_summary(env.Lp, env.an, env.threshold))
+    full = _host_ms(lambda: P.analyze(env.Lp))
+    return {"n": int(A_h.n), "moves": done, "valid": valid, "collapses": collapses,
+            "levels": [int(L0), int(env.nlevels)], "ms_per_move": 1e3 * dt / max(done, 1),
+            "ms_per_move_median": float(np.median(per_move)) if per_move else None,
+            "ms_per_move_max": float(np.max(per_move)) if per_move else None,
+            "last_move_ms": {"rewrite_list": rw, "analyze_incremental": inc, "level_summary": summ,
+                             "analyze_full_for_comparison": full}}
+
+
 def run_extras(P, items, mats, dev, bf_total):
     """Plain level-set baseline, a single-system comparison and the CPU
     oracle, all on rank 0."""
@@ -659,37 +759,17 @@ def run_extras(P, items, mats, dev, bf_total):
         "gbs": nbytes / (ms * 1e-3) / 1e9, "solves_per_s": len(sub) / (ms * 1e-3),
         "ms": ms, "sample": f"{len(sub)} of {len(items)} systems (every 16th), forward only, "
                             "original DAG, one kernel launch per level, host loop over systems",
-        "levels_launched": int(sum(p.info()["nlevels"] for p in plans))}
+        "levels_launched": int(sum(p.info()["nlevels"] for p in plans)),
+        "frac": nbytes / (ms * 1e-3) / 1e9 / hbm_peak()[0], "frac_of": "HBM peak (same as roofline.peak)"}
     del plans
-    # --- single system: 2D Laplacian 1024^2, FP64, every mode, original and rewritten
-    A_h = S.lap2d(1024)
-    A = P.Matrix.from_host(A_h, device=dev)
-    an = P.analyze(A)
-    rows, tg = S.narrowest_levels_list(an.nlevels, an.level_ptr.cpu().numpy(), an.perm.cpu().numpy(), 0.01, 8)
-    Lp, T = P.rewrite(A, an.lev, rows, tg)
-    an2 = P.analyze(Lp)
-    b = torch.as_tensor(S.rhs(A_h.n, 1, seed=1)).to(dev)
-    x = torch.empty_like(b)
-    res = {"levels_orig": an.nlevels, "levels_rewritten": an2.nlevels,
-           "cv_cost_orig": float(an.stats[3]), "cv_cost_rewritten": float(an2.stats[3]),
-           "rows_rewritten": int(len(rows)), "nnz_T": int(T.nnz), "nnz_Lp": int(Lp.nnz)}
-    modes = {}
-    for name, (M, TT) in {"orig": (A, None), "rewritten": (Lp, T)}.items():
-        p = P.Plan(M, TT)
-        nb = bytes_fwd(M.n, M.nnz, 1, 8, M.n if TT is not None else 0, TT.nnz if TT is not None else 0)
-        for mode in ("level_launch", "level", "syncfree", "block"):
-            p.set(mode, 32, 1)
-            ms = autotune.time_call(lambda: p.solve(b, out=x), reps=5, warmup=2)
-            modes[f"{name}:{mode}"] = {"us": 1e3 * ms, "gbs": nb / (ms * 1e-3) / 1e9}
-    res["fwd"] = modes
-    # analysis, rewrite and the incremental re-analysis (host-timed, each call synchronises)
-    an_ms = _host_ms(lambda: P.analyze(A))
-    rw_ms = _host_ms(lambda: P.rewrite(A, an.lev, rows, tg))
-    inc_ms = _host_ms(lambda: P.analyze(Lp, prev_lev=an.lev, first_row=int(np.min(rows))))
-    res["preprocess_ms"] = {"analyze": an_ms, "rewrite_1pct": rw_ms, "analyze_incremental_after_rewrite": inc_ms,
-                            "analyze_gbs": (A.nnz * 8 + (A.n + 1) * 4 + A.n * 4) / (an_ms * 1e-3) / 1e9}
-    out["single_lap2d_1024_f64"] = res
+    # --- single system: 2D Laplacian 1024^2, FP64 and FP32, every mode, original and rewritten
+    out["single_lap2d_1024_f64"] = _lap2d_config(P, dev, np.float64, autotune)
+    out["single_lap2d_1024_f32"] = _lap2d_config(P, dev, np.float32, autotune)
+    out["env_step_lap2d_1024"] = _env_config(P, S.lap2d(1024), dev, moves=30)
     out["powerlaw_4M_f64"] = _single_config(P, S.powerlaw(4_000_000, alpha=2.1, seed=2), dev, 1, autotune)
+    # the nnz-matched variant of the power-law DAG (mean ~9 off-diagonals per row)
+    out["powerlaw_4M_alpha1.7_f64"] = _single_config(P, S.powerlaw(4_000_000, alpha=1.7, seed=2), dev, 1, autotune,
+                                                     modes=("level", "syncfree"))
     out["lap3d_128_f64_diff_k8"] = _diff_config(P, S.lap3d(128), dev, 8, autotune)
     # --- CPU oracle on the host cores (whole batch, fwd + adjoint, one pass)
     t0 = time.perf_counter()

@@ -153,9 +153,10 @@ sptrsv_status sptrsv_analyze(sptrsv_handle handle, const sptrsv_csr *L, int32_t 
  * first recomputing all of them, each later one only the rows with a
  * predecessor changed in the round before, until a round changes nothing
  * (one launch, the environment step of the paper's Section 4.1: a rewrite
- * usually moves one row).  A change that propagates through more than 64
- * rounds (a level that empties renumbers every later level) is finished by
- * the full sync-free pass from its first unsettled row.  Then perm,
+ * usually moves one row).  A change that propagates through more than 32
+ * rounds (a level that empties renumbers every later level), or that moves
+ * more than 1024 rows in one round (a bulk rewrite), is finished by the
+ * full sync-free pass from its first unsettled row.  Then perm,
  * level_ptr, level_cost, *nlevels and stats as sptrsv_analyze.  first_row
  * outside [0, n] is SPTRSV_EINVAL; first_row = 0 is sptrsv_analyze.  The
  * results equal sptrsv_analyze's when the entry levels are right; wrong

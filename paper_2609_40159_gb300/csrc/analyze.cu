@@ -210,56 +210,149 @@ __device__ bool grid_sync(unsigned *arrive, unsigned *gen, unsigned nblocks, con
 }
 
 constexpr int kUpdThreads = 256;
+// rows changed in one round beyond which the rounds stop (a bulk change, e.g.
+// a rewrite of many rows, propagates over many rounds of full passes)
+constexpr int kUpdWideFront = 1024;
+// candidate windows up to this many rows are scanned by one block (block
+// barriers between rounds instead of grid-wide ones), for at most
+// kUpdBlockRounds rounds
+constexpr int kUpdNarrow = 8192;
+constexpr int kUpdBlockRounds = 1 << 15;
+
+// One round over the candidate rows [lo, hi) (stride over `nth` threads from
+// `tid`): a row whose predecessors changed in round r - 1 or later (every row
+// in round 1) is recomputed; returns this thread's count of changed rows and
+// the smallest / largest of them.  In round 1 also the largest span
+// i - (first column of row i), which bounds how far a change can reach.
+__device__ __forceinline__ void upd_round(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, int lo,
+                                          int hi, int64_t tid, int64_t nth, int r, int32_t *lev, int32_t *stamp,
+                                          int &cnt, int &mn, int &mx, int &span)
+{
+    for (int64_t ii = lo + tid; ii < hi; ii += nth) {
+        const int i = (int)ii;
+        const int a = ldro(rp + i), e = ldro(rp + i + 1) - 1;
+        if (r == 1 && e > a) span = max(span, i - ldro(ci + a));
+        bool cand = r == 1;
+        for (int p = a; p < e && !cand; ++p) cand = ld_relaxed(stamp + ldro(ci + p)) >= r - 1;
+        if (!cand) continue;
+        int m = -1;
+        for (int p = a; p < e; ++p) m = max(m, ld_relaxed(lev + ldro(ci + p)));
+        if (m + 1 != ld_relaxed(lev + i)) {
+            st_relaxed(lev + i, m + 1);
+            st_relaxed(stamp + i, r);
+            ++cnt;
+            mn = min(mn, i);
+            mx = max(mx, i);
+        }
+    }
+}
+
+// Block-wide sums / extremes of the four round values (all threads call it).
+__device__ __forceinline__ void upd_block_reduce(int &cnt, int &mn, int &mx, int &span, int *sm)
+{
+    cnt = __reduce_add_sync(SPT_FULL_MASK, (unsigned)cnt);
+    mn = __reduce_min_sync(SPT_FULL_MASK, mn);
+    mx = __reduce_max_sync(SPT_FULL_MASK, mx);
+    span = __reduce_max_sync(SPT_FULL_MASK, span);
+    __syncthreads();
+    if (threadIdx.x == 0) { sm[0] = 0; sm[1] = INT_MAX; sm[2] = -1; sm[3] = 0; }
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(sm, cnt);
+        atomicMin(sm + 1, mn);
+        atomicMax(sm + 2, mx);
+        atomicMax(sm + 3, span);
+    }
+    __syncthreads();
+    cnt = sm[0];
+    mn = sm[1];
+    mx = sm[2];
+    span = sm[3];
+}
 
 // Levels after a change confined to rows >= first_row, as a fixpoint of
 // lev[i] = 1 + max over predecessors (0 without), starting from the levels
 // before the change (valid for every row < first_row).  Round 1 recomputes
 // every row >= first_row from the current values; round r > 1 only the rows
 // with a predecessor whose level changed in round r - 1 or later
-// (stamp[j] = last round in which lev[j] changed, 0 = never).  A round that
-// changes nothing ends the loop: then every row satisfies the recurrence,
-// whose solution on a DAG is unique.  cnt[r] / minrow[r] receive the number
-// of rows changed in round r and the smallest of them; after max_rounds
-// rounds with changes the host finishes from minrow[max_rounds] with the
-// sync-free pass (every row below it is final).  One launch with grid-wide
-// barriers between rounds (cooperative launch: all blocks resident).
+// (stamp[j] = last round in which lev[j] changed, 0 = never), which lie in
+// the window (smallest changed row, largest changed row + span]: span, the
+// largest distance from a row to its first column, bounds how far a row's
+// successors are.  A round that changes nothing ends the loop: then every row
+// satisfies the recurrence, whose solution on a DAG is unique.  Rounds run
+// over the whole grid with grid-wide barriers; once the window is narrow, one
+// block continues alone with block barriers (a change that travels along a
+// chain of single dependencies, e.g. the boundary of a grid, moves one row per
+// round).  The rounds give up -- res = {2, smallest row changed in the last
+// round}, every row below it final, the host finishes with the sync-free
+// pass -- after max_rounds grid rounds, kUpdBlockRounds block rounds, on a
+// round that changes more than kUpdWideFront rows, or when a block round's
+// window grows wide; res = {1, n} at the fixpoint.  Cooperative launch (every
+// block resident).
 __global__ void __launch_bounds__(kUpdThreads)
 k_levels_update(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, int32_t n, int32_t first_row,
-                int32_t *lev, int32_t *stamp, int32_t *cnt, int32_t *minrow, unsigned *bar, int max_rounds,
-                Waiter w, int32_t withhold)
+                int32_t *lev, int32_t *stamp, int32_t *cnt, int32_t *minrow, int32_t *maxrow, int32_t *span_max,
+                int32_t *res, unsigned *bar, int max_rounds, Waiter w, int32_t withhold)
 {
-    __shared__ int s_cnt, s_min;
+    __shared__ int sm[4];
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t nth = (int64_t)gridDim.x * blockDim.x;
-    for (int r = 1; r <= max_rounds; ++r) {
-        if (threadIdx.x == 0) { s_cnt = 0; s_min = INT_MAX; }
-        __syncthreads();
-        int my_cnt = 0, my_min = INT_MAX;
-        for (int64_t ii = first_row + tid; ii < n; ii += nth) {
-            const int i = (int)ii;
-            const int a = ldro(rp + i), e = ldro(rp + i + 1) - 1;
-            bool cand = r == 1;
-            for (int p = a; p < e && !cand; ++p) cand = ld_relaxed(stamp + ldro(ci + p)) >= r - 1;
-            if (!cand) continue;
-            int m = -1;
-            for (int p = a; p < e; ++p) m = max(m, ld_relaxed(lev + ldro(ci + p)));
-            if (m + 1 != ld_relaxed(lev + i)) {
-                st_relaxed(lev + i, m + 1);
-                st_relaxed(stamp + i, r);
-                ++my_cnt;
-                my_min = min(my_min, i);
-            }
+    int lo = first_row, hi = n;
+    int r = 1;
+    for (; r <= max_rounds; ++r) {
+        int c = 0, mn = INT_MAX, mx = -1, span = 0;
+        upd_round(rp, ci, lo, hi, tid, nth, r, lev, stamp, c, mn, mx, span);
+        upd_block_reduce(c, mn, mx, span, sm);
+        if (threadIdx.x == 0 && c) {
+            atomicAdd(cnt + r, c);
+            atomicMin(minrow + r, mn);
+            atomicMax(maxrow + r, mx);
         }
-        my_cnt = __reduce_add_sync(SPT_FULL_MASK, (unsigned)my_cnt);
-        my_min = __reduce_min_sync(SPT_FULL_MASK, my_min);
-        if ((threadIdx.x & 31) == 0 && my_cnt) { atomicAdd(&s_cnt, my_cnt); atomicMin(&s_min, my_min); }
-        __syncthreads();
-        if (threadIdx.x == 0 && s_cnt) { atomicAdd(cnt + r, s_cnt); atomicMin(minrow + r, s_min); }
+        if (threadIdx.x == 0 && r == 1) atomicMax(span_max, span);
         // test hook: the first block never arrives at the first barrier
         if (withhold >= 0 && blockIdx.x == 0) return;
         if (!grid_sync(bar, bar + 1, gridDim.x, w)) return;
-        if (ld_relaxed(cnt + r) == 0) return;  // uniform: read after the barrier
+        // uniform from here on (values read after the barrier)
+        const int changed = ld_relaxed(cnt + r);
+        if (changed == 0) {
+            if (tid == 0) { res[0] = 1; res[1] = n; }
+            return;
+        }
+        if (changed > kUpdWideFront) {
+            if (tid == 0) { res[0] = 2; res[1] = ld_relaxed(minrow + r); }
+            return;
+        }
+        lo = ld_relaxed(minrow + r) + 1;
+        const int64_t h = (int64_t)ld_relaxed(maxrow + r) + ld_relaxed(span_max) + 1;
+        hi = (int)(h < (int64_t)n ? h : (int64_t)n);
+        if (hi - lo <= kUpdNarrow) { ++r; break; }
     }
+    if (r > max_rounds) {
+        if (tid == 0) { res[0] = 2; res[1] = ld_relaxed(minrow + max_rounds); }
+        return;
+    }
+    // narrow window: block 0 continues alone
+    if (blockIdx.x != 0) return;
+    const int span = ld_relaxed(span_max);
+    int last_min = lo - 1;
+    for (int rr = r; rr < r + kUpdBlockRounds; ++rr) {
+        int c = 0, mn = INT_MAX, mx = -1, sp = 0;
+        upd_round(rp, ci, lo, hi, threadIdx.x, blockDim.x, rr, lev, stamp, c, mn, mx, sp);
+        upd_block_reduce(c, mn, mx, sp, sm);  // ends with a block barrier: this round's writes are visible
+        if (c == 0) {
+            if (threadIdx.x == 0) { res[0] = 1; res[1] = n; }
+            return;
+        }
+        last_min = mn;
+        lo = mn + 1;
+        const int64_t h2 = (int64_t)mx + span + 1;
+        hi = (int)(h2 < (int64_t)n ? h2 : (int64_t)n);
+        if (c > kUpdWideFront || hi - lo > kUpdNarrow) break;
+        // the block barrier orders this round's relaxed stores before the
+        // next round's loads for the block's own threads (CTA scope)
+        __threadfence_block();
+    }
+    if (threadIdx.x == 0) { res[0] = 2; res[1] = last_min; }
 }
 
 __global__ void k_count_long(const int32_t *rp, int32_t n, int32_t min_offdiag, unsigned long long *out)
@@ -472,16 +565,19 @@ cudaError_t launch_levels_update(const sptrsv_csr &L, int32_t first_row, int32_t
     *restart_row = L.n;
     const int64_t rows = (int64_t)L.n - first_row;
     if (rows <= 0) return cudaSuccess;
-    // scratch: stamp[n], cnt[R+1], minrow[R+1], barrier {count, generation}
+    // scratch: stamp[n], cnt[R+1], minrow[R+1], maxrow[R+1], span, res[2],
+    // barrier {count, generation}
     const size_t nstamp = (size_t)L.n, nr = (size_t)max_rounds + 1;
     int32_t *buf = nullptr;
-    cudaError_t e = cudaMallocAsync(&buf, sizeof(int32_t) * (nstamp + 2 * nr + 2), s);
+    cudaError_t e = cudaMallocAsync(&buf, sizeof(int32_t) * (nstamp + 3 * nr + 5), s);
     if (e != cudaSuccess) return e;
-    int32_t *stamp = buf, *cnt = buf + nstamp, *minrow = cnt + nr;
-    unsigned *bar = reinterpret_cast<unsigned *>(minrow + nr);
+    int32_t *stamp = buf, *cnt = buf + nstamp, *minrow = cnt + nr, *maxrow = minrow + nr;
+    int32_t *span = maxrow + nr, *res = span + 1;
+    unsigned *bar = reinterpret_cast<unsigned *>(res + 2);
     e = cudaMemsetAsync(stamp, 0, sizeof(int32_t) * (nstamp + nr), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(minrow, 0x7f, sizeof(int32_t) * nr, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(maxrow, 0xff, sizeof(int32_t) * nr, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(span, 0, sizeof(int32_t) * 5, s);
     int per_sm = 0;
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_levels_update, kUpdThreads, 0);
     if (e == cudaSuccess) {
@@ -490,22 +586,21 @@ cudaError_t launch_levels_update(const sptrsv_csr &L, int32_t first_row, int32_t
         Waiter w{ctl.status, ctl.abort_flag, limit_ns};
         int32_t n = L.n;
         const int32_t *rp = L.row_ptr, *ci = L.col_idx;
-        void *args[] = {(void *)&rp, (void *)&ci, (void *)&n, (void *)&first_row, (void *)&lev, (void *)&stamp,
-                        (void *)&cnt, (void *)&minrow, (void *)&bar, (void *)&max_rounds, (void *)&w,
-                        (void *)&withhold};
+        void *args[] = {(void *)&rp,     (void *)&ci,     (void *)&n,    (void *)&first_row, (void *)&lev,
+                        (void *)&stamp,  (void *)&cnt,    (void *)&minrow, (void *)&maxrow, (void *)&span,
+                        (void *)&res,    (void *)&bar,    (void *)&max_rounds, (void *)&w, (void *)&withhold};
         e = cudaLaunchCooperativeKernel((const void *)k_levels_update, dim3((unsigned)grid), dim3(kUpdThreads),
                                         args, 0, s);
     }
-    std::vector<int32_t> hc(nr), hm(nr);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(hc.data(), cnt, sizeof(int32_t) * nr, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(hm.data(), minrow, sizeof(int32_t) * nr, cudaMemcpyDeviceToHost, s);
+    int32_t hres[2] = {0, 0};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hres, res, sizeof(hres), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     cudaFreeAsync(buf, s);
     if (e != cudaSuccess) return e;
-    bool done = false;
-    for (int r = 1; r <= max_rounds && !done; ++r) done = hc[r] == 0;
-    *converged = done;
-    if (!done) *restart_row = hm[max_rounds];
+    // res = {1, n}: fixpoint; {2, row}: rows below `row` are final; {0, 0}:
+    // the launch gave up (bounded wait; the abort flag says so) -- start over
+    *converged = hres[0] == 1;
+    *restart_row = hres[0] == 2 ? hres[1] : (hres[0] == 1 ? L.n : 0);
     return cudaSuccess;
 }
 

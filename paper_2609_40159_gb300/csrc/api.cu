@@ -23,7 +23,7 @@ struct Range {
     ~Range() { nvtxRangePop(); }
 };
 constexpr long long kDefaultWaitNs = 10ll * 1000 * 1000 * 1000;  // 10 s
-constexpr int kUpdateRounds = 64;  // fixpoint rounds of an incremental analysis before the full pass
+constexpr int kUpdateRounds = 32;  // fixpoint rounds of an incremental analysis before the full pass
 
 bool debug_mode()
 {
@@ -273,7 +273,8 @@ sptrsv_status levels_impl(sptrsv_handle h, const sptrsv_csr &L, int32_t *lev, in
         // after a change confined to rows >= first_row: fixpoint rounds from
         // the previous levels; a change that propagates through more than
         // kUpdateRounds rounds (a level collapse renumbers every later level)
-        // is finished by the sync-free pass from the first unsettled row
+        // or moves many rows at once is finished by the sync-free pass from
+        // the first unsettled row
         bool converged = false;
         e = launch_levels_update(L, first_row, lev, ctl, spin, h->di, s, kUpdateRounds, h->dbg_withhold,
                                  &converged, &restart);
