@@ -166,7 +166,7 @@ sptrsv_status sptrsv_analyze_incremental(sptrsv_handle handle, const sptrsv_csr 
                                          int64_t *level_cost, int32_t *nlevels, double stats[6]);
 
 /* What the paper's environment observes after each rewrite (Section 4.1:
- * thin levels; Section 4.2: the node a move takes from a level is the one
+ * thin levels; Section 4.3: the node a move takes from a level is the one
  * with the fewest dependencies), from an analysis of L:
  *   perm, level_ptr, level_cost, nlevels  as returned by sptrsv_analyze
  *                 (device arrays);

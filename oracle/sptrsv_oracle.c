@@ -10,7 +10,7 @@
  *   - Section 2.2: equation rewriting replaces a row's dependencies by their
  *     predecessors so that the row moves to an earlier level; it is a
  *     preprocessing step and the result is again a CSR lower-triangular system.
- *   - Section 3 / Tables 4-5: level cost, ALC, ARL, AIR; Section 4.1 and
+ *   - Section 4.1 / Tables 4-5: level cost, ALC, ARL, AIR; Section 4.1 and
  *     Table 1: coefficient of variation of level costs and node counts, and
  *     the thin-level threshold ALC * (1 + alpha * max(0, 1 - CV)).
  *
@@ -199,12 +199,12 @@ double orc_thin_threshold(double alc, double cv, double alpha)
 }
 
 /* Level summary that the paper's environment observes after every rewrite
- * (Section 4.1 and Section 4.2, Tables 4-5):
+ * (Section 4.1 and Section 4.3, Tables 4-5):
  *   thin[l]  = 1 when cost[l] < threshold (a thin level: its cost is below
  *              the thin-level threshold), else 0;
  *   pick[l]  = the row of level l with the smallest number of dependencies
  *              (off-diagonals), the smallest row index among equals -- the
- *              node a rewrite of level l moves (Section 4.2);
+ *              node a rewrite of level l moves (Section 4.3);
  *   out[0] number of thin levels, out[1] largest row count of a thin level,
  *   out[2] largest cost of a thin level (0 when there is none).
  * The cost comparison is in double, as the threshold.                    */
@@ -267,7 +267,7 @@ void orc_stats(int32_t n, int64_t nnz, int32_t nlevels, const int32_t *level_ptr
 }
 
 /* ---------------------------------------------------------------------- */
-/* Equation rewriting (Section 2.2; rewriting list of Section 4.4): textbook
+/* Equation rewriting (Section 2.2; rewriting list of Section 4.3): textbook
  * row substitution.  For a listed row i with target level t < lev(i):
  *
  *   acc <- row i (off-diagonals, column -> value);  tb <- {}

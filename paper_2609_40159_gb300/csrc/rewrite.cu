@@ -1,5 +1,5 @@
 // Equation rewriting on the GPU (paper Section 2.2; rewriting list of
-// Section 4.4).  For a listed row i with target level t, every predecessor j
+// Section 4.3).  For a listed row i with target level t, every predecessor j
 // with lev(j) >= t is substituted, largest column first, by row j's own
 // predecessors scaled by m = acc[j] / L_jj (original rows, original levels);
 // the right-hand side picks up T[i][j] = -m.  The result is L' x = b + T b.

@@ -377,7 +377,7 @@ def batch_spec_parallel(nmat: int = 512, seed: int = 3, workers: int | None = No
 # ----------------------------------------------------------------------------
 # Rewrite lists.  These stand in for the rewriting list that the paper's
 # policy (or its heuristic strategies) hands to the rewriting module
-# (Section 4.4: triplets <node, source level, target level>).  They read the
+# (Section 4.3: triplets <node, source level, target level>).  They read the
 # level partition produced by an analysis; they compute nothing of the method.
 # ----------------------------------------------------------------------------
 
