@@ -276,6 +276,28 @@ sptrsv_status sptrsv_batch_plan_set(sptrsv_plan plan, const int32_t *rows_per_wa
  * times and sets each on its own.  Synchronises.                          */
 sptrsv_status sptrsv_batch_plan_set_direction(sptrsv_plan plan, int32_t direction,
                                               const int32_t *rows_per_warp, const int32_t *rhs_tile);
+/* Schedule of each system's work items (Section 2.1: the level-set
+ * schedule, and the synchronisation-free alternative of the related work),
+ * for one direction as above (0 = both):
+ *   schedule  host, nmat entries:
+ *     SPTRSV_BATCH_INORDER  rows in row order, groups of 32 rows completed
+ *                           one after another, dependencies inside a group
+ *                           resolved in registers (the default);
+ *     SPTRSV_BATCH_LEVEL    rows in level order (the plan's analysis; the
+ *                           transpose solve takes the levels last to
+ *                           first), groups of at most 32 rows of one
+ *                           level, every group of a level at the same
+ *                           time, each level after the previous one;
+ *     0                     keep.
+ * The first switch of a system to SPTRSV_BATCH_LEVEL builds its tables
+ * (inverse permutation: 4 bytes per row; 16 bytes per group).  Returns
+ * SPTRSV_EINVAL for another value, SPTRSV_ENOTSUP when the geometry does
+ * not fit in shared memory (the previous schedules are kept).
+ * Synchronises.                                                           */
+#define SPTRSV_BATCH_INORDER 1
+#define SPTRSV_BATCH_LEVEL 2
+sptrsv_status sptrsv_batch_plan_set_schedule(sptrsv_plan plan, int32_t direction,
+                                             const int32_t *schedule);
 /* All systems in one persistent launch (plus a tiny reset launch; the
  * transpose solve also gathers the values into CSC order first): no host
  * work per matrix, so the call can be captured in a CUDA graph.            */

@@ -106,6 +106,7 @@ _SIGS = {
     "sptrsv_batch_offsets": [sptrsv_plan, _PI64, _PI64],
     "sptrsv_batch_plan_set": [sptrsv_plan, _PI32, _PI32],
     "sptrsv_batch_plan_set_direction": [sptrsv_plan, _I32, _PI32, _PI32],
+    "sptrsv_batch_plan_set_schedule": [sptrsv_plan, _I32, _PI32],
     "sptrsv_batch_solve": [sptrsv_plan, _P, _P],
     "sptrsv_batch_solve_transpose": [sptrsv_plan, _P, _P],
     "sptrsv_batch_grad_vals": [sptrsv_plan, _P, _P, _P],
@@ -116,6 +117,8 @@ _SIGS = {
     "sptrsv_solve_noalloc": [C.POINTER(sptrsv_csr), _P, _P, _I32, _I64, _P],
 }
 SPTRSV_NOALLOC_MAX_ROWS = 1 << 20
+SPTRSV_BATCH_INORDER = 1
+SPTRSV_BATCH_LEVEL = 2
 
 DECLARED = sorted(list(_SIGS) + ["sptrsv_status_string"])
 

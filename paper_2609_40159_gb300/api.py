@@ -382,6 +382,18 @@ class BatchPlan:
         L.check(L.lib().sptrsv_batch_plan_set_direction(self.p, d, arr(rows_per_warp), arr(rhs_tile)),
                 "sptrsv_batch_plan_set_direction")
 
+    def set_schedule(self, schedule, direction="both"):
+        """Schedule of each system's work items, per system (list) or for
+        all systems: "inorder" (rows in row order, 32-row groups one after
+        another), "level" (rows in level order, the groups of a level at the
+        same time), or None (keep); direction as in set_geometry."""
+        nmat = len(self.mats)
+        code = {None: 0, "inorder": L.SPTRSV_BATCH_INORDER, "level": L.SPTRSV_BATCH_LEVEL}
+        vals = schedule if isinstance(schedule, (list, tuple)) else [schedule] * nmat
+        arr = (C.c_int32 * max(nmat, 1))(*[code[v] for v in vals])
+        d = {"both": 0, "forward": 1, "transpose": 2}[direction]
+        L.check(L.lib().sptrsv_batch_plan_set_schedule(self.p, d, arr), "sptrsv_batch_plan_set_schedule")
+
     def set_rows_per_warp(self, rpw):
         """Row-group width per system (list) or for all systems (int)."""
         self.set_geometry(rows_per_warp=rpw)

@@ -117,14 +117,15 @@ def batch_classes(bplan: BatchPlan):
 
 
 def tune_batch(bplan: BatchPlan, b: torch.Tensor, candidates=(8, 16, 32), tiles=(2, 4, 8), reps=3,
-               rounds=1, direction="forward"):
-    """Rows-per-warp and right-hand-side tile of the batched solve in one
-    direction ("forward": the solve; "transpose": the transpose solve of
-    the adjoint, which has its own geometry and its own timing).  The batch
-    time is a makespan, so the search first sets one tile width for every
-    system, then refines per size class (coordinate descent: each class
-    tries every candidate of one knob with everything else fixed).  A
-    rows-per-warp of 0 keeps the plan's default for that system."""
+               rounds=1, direction="forward", schedules=("inorder", "level")):
+    """Rows-per-warp, right-hand-side tile and schedule (in row order or
+    level by level) of the batched solve in one direction ("forward": the
+    solve; "transpose": the transpose solve of the adjoint, which has its
+    own geometry and its own timing).  The batch time is a makespan, so the
+    search first sets one tile width for every system, then refines per
+    size class (coordinate descent: each class tries every candidate of one
+    knob with everything else fixed).  A rows-per-warp of 0 keeps the plan's
+    default for that system; the level schedule ignores it."""
     if direction not in ("forward", "transpose"):
         raise ValueError("direction must be 'forward' or 'transpose'")
     labels = batch_classes(bplan)
@@ -135,6 +136,7 @@ def tune_batch(bplan: BatchPlan, b: torch.Tensor, candidates=(8, 16, 32), tiles=
 
     def apply(choice):
         bplan.set_geometry([choice[l][0] for l in labels], [choice[l][1] for l in labels], direction=direction)
+        bplan.set_schedule([choice[l][2] for l in labels], direction=direction)
 
     def measure(choice):
         try:
@@ -145,7 +147,7 @@ def tune_batch(bplan: BatchPlan, b: torch.Tensor, candidates=(8, 16, 32), tiles=
 
     best, best_ms = None, float("inf")
     for t in tiles:
-        choice = {c: [0, t] for c in classes}
+        choice = {c: [0, t, "inorder"] for c in classes}
         ms = measure(choice)
         log.append(dict(step="uniform", rhs_tile=t, ms=ms))
         if ms is not None and ms < best_ms:
@@ -155,17 +157,18 @@ def tune_batch(bplan: BatchPlan, b: torch.Tensor, candidates=(8, 16, 32), tiles=
     choice = best
     for _ in range(rounds):
         for c in classes:
-            for knob, cands in ((0, candidates), (1, tiles)):
+            for knob, cands in ((0, candidates), (1, tiles), (2, schedules)):
                 keep = choice[c][knob]
                 for cand in cands:
                     if cand == keep:
                         continue
                     choice[c][knob] = cand
                     ms = measure(choice)
-                    log.append(dict(cls=c, knob=("rows_per_warp", "rhs_tile")[knob], value=cand, ms=ms))
+                    log.append(dict(cls=c, knob=("rows_per_warp", "rhs_tile", "schedule")[knob], value=cand, ms=ms))
                     if ms is not None and ms < best_ms * 0.995:
                         best_ms, keep = ms, cand
                 choice[c][knob] = keep
     apply(choice)
-    return dict(choice={c: dict(rows_per_warp=v[0], rhs_tile=v[1]) for c, v in choice.items()}, ms=best_ms,
+    return dict(choice={c: dict(rows_per_warp=v[0], rhs_tile=v[1], schedule=v[2]) for c, v in choice.items()},
+                ms=best_ms,
                 log=log, direction=direction)

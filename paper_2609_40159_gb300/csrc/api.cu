@@ -100,6 +100,11 @@ struct PlanMat {
     int32_t *d_cp = nullptr, *d_crow = nullptr, *d_tmap = nullptr;
     void *d_cv = nullptr;  // L's values in CSC order (transpose solves)
     uint32_t *d_tmask = nullptr;
+    // level-ordered batched schedule (built when first used): inverse of
+    // d_perm, row groups of each direction
+    int32_t *d_iperm = nullptr;
+    LevelGroup *d_lgroups[2] = {nullptr, nullptr};
+    int32_t n_lgroups[2] = {0, 0};
 };
 
 struct sptrsv_plan_st {
@@ -128,7 +133,7 @@ struct sptrsv_plan_st {
     // rows per warp and rhs columns per work item, the items (system, rhs
     // column tile, geometry), their launch order, shared memory and grid
     struct Geom {
-        std::vector<int32_t> rpw, tile;
+        std::vector<int32_t> rpw, tile, sched;
         BatchItem *d_items = nullptr;
         int32_t *d_order = nullptr;
         int32_t nitems = 0;
@@ -753,15 +758,22 @@ sptrsv_status rebuild_items(sptrsv_plan p, int dir)
             I.r0 = r0;
             I.kt = std::min(tile, k - r0);
             I.KT = pow2_at_least(I.kt);
-            I.rpw = G.rpw[m];
-            I.nw = std::min(kBatchWarps,
-                            block_warps_for(M.nlevels > 0 ? (double)M.L.n / M.nlevels : 1.0, I.rpw));
+            I.sched = G.sched[m];
+            I.rpw = I.sched == kSchedLevel ? 32 : G.rpw[m];
+            I.nw = I.sched == kSchedLevel
+                       ? kBatchWarps
+                       : std::min(kBatchWarps,
+                                  block_warps_for(M.nlevels > 0 ? (double)M.L.n / M.nlevels : 1.0, I.rpw));
             block_geometry(I.rpw, I.KT, f64, I.nw, &I.kc, &I.P, kBatchSmemGrow);
             smem = std::max(smem, block_smem_bytes(I.rpw, I.KT, I.kc, f64, I.nw));
             items.push_back(I);
-            // chain of n / 32 row groups whose cost grows with the tile width,
-            // plus the streamed matrix
-            est.push_back((double)M.L.n * (1.0 + 0.1 * I.KT) + 0.01 * (double)M.L.nnz);
+            // in order: a chain of n / 32 row groups whose cost grows with
+            // the tile width; level-ordered: a chain of one or more groups per
+            // level (each about a third of an in-order group); plus the
+            // streamed matrix
+            const double chain = I.sched == kSchedLevel ? 12.0 * (double)M.nlevels + 0.1 * (double)M.L.n
+                                                        : (double)M.L.n;
+            est.push_back(chain * (1.0 + 0.1 * I.KT) + 0.01 * (double)M.L.nnz);
         }
     }
     if (smem > kBlockSmemBudget) return SPTRSV_ENOTSUP;
@@ -779,6 +791,81 @@ sptrsv_status rebuild_items(sptrsv_plan p, int dir)
     G.nitems = ni;
     G.smem = smem;
     G.grid = std::min(batch_grid(smem, p->h->di), std::max(ni, 1));
+    return SPTRSV_OK;
+}
+
+// Tables of the level-ordered schedule of system m in direction dir: the
+// inverse permutation (once per system) and the row groups: every level's
+// positions cut into groups of at most 32, in level order (forward) or in
+// reverse level order (transpose), each with the number of groups of the
+// levels before it in that order.
+sptrsv_status ensure_level_tables(sptrsv_plan p, int m, int dir)
+{
+    PlanMat &M = p->mats[m];
+    const int32_t n = M.L.n;
+    cudaError_t e = cudaSuccess;
+    if (!M.d_iperm) {
+        e = p->alloc(&M.d_iperm, sizeof(int32_t) * (size_t)std::max(n, 1));
+        if (e == cudaSuccess) e = inverse_perm(M.d_perm, M.d_iperm, n, p->h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(p->h->stream);
+        if (e != cudaSuccess) return from_cuda(e);
+    }
+    if (!M.d_lgroups[dir]) {
+        std::vector<LevelGroup> g;
+        const int32_t L = M.nlevels;
+        const std::vector<int32_t> &lp = M.h_level_ptr;
+        for (int32_t k = 0; k < L; ++k) {
+            const int32_t l = dir == 0 ? k : L - 1 - k;
+            // positions of level l in this direction's order
+            const int32_t s = dir == 0 ? lp[l] : n - lp[l + 1];
+            const int32_t t = dir == 0 ? lp[l + 1] : n - lp[l];
+            const int32_t first = (int32_t)g.size();
+            for (int32_t q = s; q < t; q += 32) g.push_back(LevelGroup{q, std::min(32, t - q), t, first});
+        }
+        e = p->alloc(&M.d_lgroups[dir], sizeof(LevelGroup) * std::max<size_t>(g.size(), 1));
+        if (e == cudaSuccess && !g.empty())
+            e = cudaMemcpy(M.d_lgroups[dir], g.data(), sizeof(LevelGroup) * g.size(), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return from_cuda(e);
+        M.n_lgroups[dir] = (int32_t)g.size();
+    }
+    BatchMat &B = p->h_mats[m];
+    B.perm = M.d_perm;
+    B.iperm = M.d_iperm;
+    B.lgroups[dir] = M.d_lgroups[dir];
+    B.nlgroups[dir] = M.n_lgroups[dir];
+    e = cudaStreamSynchronize(p->h->stream);
+    if (e == cudaSuccess) e = cudaMemcpy(p->d_mats + m, &B, sizeof(BatchMat), cudaMemcpyHostToDevice);
+    return from_cuda(e);
+}
+
+// New per-system schedules (SPTRSV_BATCH_INORDER / _LEVEL; 0 keeps) for the
+// directions in `dirs`.
+sptrsv_status set_schedule(sptrsv_plan p, int dirs, const int32_t *schedule)
+{
+    const int32_t nmat = (int32_t)p->h_mats.size();
+    for (int m = 0; m < nmat; ++m)
+        if (schedule[m] != 0 && schedule[m] != SPTRSV_BATCH_INORDER && schedule[m] != SPTRSV_BATCH_LEVEL)
+            return SPTRSV_EINVAL;
+    for (int d = 0; d < 2; ++d) {
+        if (!((dirs >> d) & 1)) continue;
+        sptrsv_plan_st::Geom &G = p->geo[d];
+        const std::vector<int32_t> old = G.sched;
+        for (int m = 0; m < nmat; ++m) {
+            if (schedule[m] == SPTRSV_BATCH_LEVEL) {
+                sptrsv_status st = ensure_level_tables(p, m, d);
+                if (st != SPTRSV_OK) return st;
+                G.sched[m] = kSchedLevel;
+            } else if (schedule[m] == SPTRSV_BATCH_INORDER) {
+                G.sched[m] = kSchedInOrder;
+            }
+        }
+        sptrsv_status st = rebuild_items(p, d);
+        if (st == SPTRSV_ENOTSUP) {
+            G.sched = old;
+            if (rebuild_items(p, d) != SPTRSV_OK) return SPTRSV_ECUDA;
+        }
+        if (st != SPTRSV_OK) return st;
+    }
     return SPTRSV_OK;
 }
 
@@ -839,6 +926,7 @@ extern "C" sptrsv_status sptrsv_batch_plan_create(sptrsv_handle h, int32_t nmat,
     for (int d = 0; d < 2; ++d) {
         p->geo[d].rpw.assign((size_t)nmat, 32);
         p->geo[d].tile.assign((size_t)nmat, 4);
+        p->geo[d].sched.assign((size_t)nmat, kSchedInOrder);
     }
     int64_t ktot = 0;
     for (int m = 0; m < nmat; ++m) {
@@ -949,6 +1037,13 @@ extern "C" sptrsv_status sptrsv_batch_plan_set_direction(sptrsv_plan p, int32_t 
 {
     if (!p || !p->batched || direction < 0 || direction > 2) return SPTRSV_EINVAL;
     return set_geometry(p, direction == 0 ? 3 : direction, rows_per_warp, rhs_tile);
+}
+
+extern "C" sptrsv_status sptrsv_batch_plan_set_schedule(sptrsv_plan p, int32_t direction, const int32_t *schedule)
+{
+    Range range("sptrsv_batch_plan_set_schedule");
+    if (!p || !p->batched || !schedule || direction < 0 || direction > 2) return SPTRSV_EINVAL;
+    return set_schedule(p, direction == 0 ? 3 : direction, schedule);
 }
 
 extern "C" sptrsv_status sptrsv_batch_offsets(sptrsv_plan p, int64_t *rhs_offset, int64_t *vals_offset)

@@ -45,7 +45,10 @@ __device__ __forceinline__ bool run_one(const BatchMat &M, const BatchItem &I, u
     // test hook: a withheld row (counted over all systems) is never published
     const int64_t wh = (int64_t)withhold - M.row_off;
     const int local = (withhold >= 0 && wh >= 0 && wh < M.n) ? (int)wh : -1;
-    const bool ok = block_solve_any<T, KT, TR, false>(A, R, I.rpw, I.kc, I.P, I.nw, sm, w, local);
+    const bool ok = I.sched == kSchedLevel
+                        ? block_solve_levels<T, KT, TR>(A, R, M.perm, M.iperm, M.lgroups[TR ? 1 : 0],
+                                                        M.nlgroups[TR ? 1 : 0], I.kc, I.nw, sm, w, local)
+                        : block_solve_any<T, KT, TR, false>(A, R, I.rpw, I.kc, I.P, I.nw, sm, w, local);
     __syncthreads();
     release_block_smem<T, KT>(sm, I.kc);
     return ok;
@@ -241,6 +244,21 @@ int elementwise_grid(int64_t nchunks)
 }
 
 }  // namespace
+
+namespace {
+__global__ void k_inverse_perm(const int32_t *__restrict__ perm, int32_t *__restrict__ iperm, int32_t n)
+{
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x)
+        iperm[perm[q]] = (int32_t)q;
+}
+}  // namespace
+
+cudaError_t inverse_perm(const int32_t *perm, int32_t *iperm, int32_t n, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    k_inverse_perm<<<(int)std::min<int64_t>(((int64_t)n + 255) / 256, 152 * 16), 256, 0, s>>>(perm, iperm, n);
+    return cudaGetLastError();
+}
 
 int batch_grid(size_t smem, const DeviceInfo &di)
 {

@@ -526,6 +526,178 @@ __device__ bool block_solve_sweep(const Sys<T> &A, const Rhs<T> &R, int kc, int 
     return true;
 }
 
+// Block-local level-scheduled solve: the rows in level order (transpose:
+// its reverse), cut into groups of at most 32 rows of ONE level (`groups`,
+// dealt to the warps round-robin, one lane per row).  The rows of a level
+// do not depend on each other, so a group needs no in-group sweep, and the
+// groups of one level run at the same time; a group waits only until every
+// group of the earlier levels is complete (a shared counter of completed
+// groups reaches its `wait`: before that count is reached, only groups of
+// earlier levels can complete, as later ones are still waiting).  Progress:
+// the smallest incomplete group waits for smaller groups only, and its
+// warp has completed all of its earlier (smaller) groups.
+// Dependencies live in a shared-memory ring addressed by processing
+// position (slot = position mod ring).  While a group of level l runs, only
+// groups of level l write the ring, at positions below the level's end
+// `lend`; so every position q >= lend - ring still holds its own value, and
+// entries at positions below base - win (win = ring - (lend - base)) are
+// read from global memory instead.  Values, ring slots and global copies of
+// a group are written before its completion is counted (release), and a
+// waiter acquires the count, so both reads see complete values.
+template <class T, int KT, bool TR>
+__device__ bool block_solve_levels(const Sys<T> &A, const Rhs<T> &R, const int32_t *__restrict__ perm,
+                                   const int32_t *__restrict__ iperm, const LevelGroup *__restrict__ groups,
+                                   int ngroups, int kc, int nwarps, const BlockSmem<T, KT> &sm,
+                                   const Waiter &w, int withhold)
+{
+    constexpr int NP = kPreload;
+    const int lane = threadIdx.x & 31;
+    const int wid = threadIdx.x >> 5;
+    if (wid >= nwarps) return true;
+    const int n = A.n;
+    const int ring = kc * 32;  // a power of two
+    const int rmask = ring - 1;
+    const int kt = R.k;
+    const T *ring0 = const_cast<const T *>(sm.xr);
+    // row at processing position q; processing position of row j
+    auto row_at = [&](int q) { return ldro(perm + (TR ? n - 1 - q : q)); };
+    auto pos_of = [&](int j) {
+        const int p = ldro(iperm + j);
+        return TR ? n - 1 - p : p;
+    };
+    // a warp's next group, its rows and their extents are loaded one group
+    // ahead, and the group after it one more ahead, so that a group's
+    // entries are one dependent load away when it starts
+    LevelGroup gn{0, 0, 0, 0}, gnn{0, 0, 0, 0};
+    int i_nx = 0, a_nx = 0, e_nx = 0;
+    if (wid < ngroups) {
+        gn = groups[wid];
+        i_nx = row_at(gn.base + (lane < gn.cnt ? lane : 0));
+        a_nx = RV<T, TR>::beg(A, i_nx);
+        e_nx = RV<T, TR>::end(A, i_nx);
+    }
+    if (wid + nwarps < ngroups) gnn = groups[wid + nwarps];
+    for (int g = wid; g < ngroups; g += nwarps) {
+        const LevelGroup G = gn;
+        const int i = i_nx, a = a_nx, e = e_nx;
+        if (g + nwarps < ngroups) {
+            gn = gnn;
+            i_nx = row_at(gn.base + (lane < gn.cnt ? lane : 0));
+            a_nx = RV<T, TR>::beg(A, i_nx);
+            e_nx = RV<T, TR>::end(A, i_nx);
+            if (g + 2 * nwarps < ngroups) gnn = groups[g + 2 * nwarps];
+        }
+        const int base = G.base;
+        const bool valid = lane < G.cnt;
+        const int pos = base + (valid ? lane : 0);
+        // ---- 1. independent of the solution
+        const int safe = TR ? a - 1 : e;  // position of the diagonal entry
+        const T rinv = valid ? T(1) / RV<T, TR>::diag(A, a, e) : T(0);
+        T acc[KT], bv[KT];
+#pragma unroll
+        for (int r = 0; r < KT; ++r) {
+            acc[r] = T(0);
+            bv[r] = (valid && r < kt) ? R.b[(int64_t)i * R.ld + r] : T(0);
+        }
+        if (!TR && valid && has_trow(A, i)) {
+            for (int p = A.trp[i]; p < A.trp[i + 1]; ++p) {
+                const T tv = ldro(A.tv + p);
+                const T *bb = R.b + (int64_t)ldro(A.tci + p) * R.ld;
+#pragma unroll
+                for (int r = 0; r < KT; ++r)
+                    if (r < kt) acc[r] -= tv * bb[r];
+            }
+        }
+        int jj[NP];
+        T vv[NP];
+#pragma unroll
+        for (int u = 0; u < NP; ++u) {
+            const int q = a + u < e ? a + u : safe;
+            jj[u] = pos_of(RV<T, TR>::col(A, q));
+            vv[u] = RV<T, TR>::val(A, q);
+        }
+        // ring window of this group (see above)
+        const int win = max(0, ring - (G.lend - base));
+        const int lo = base - win;
+        bool any_glob = false;
+#pragma unroll
+        for (int u = 0; u < NP; ++u) {
+            const bool in = valid && a + u < e;
+            const bool use = in && jj[u] >= lo;
+            any_glob |= in && !use;
+            // ring pass decided now: an entry in the ring keeps its value and
+            // becomes its slot's offset; any other entry reads slot 0 with
+            // weight 0 (global ones are applied separately, once complete)
+            vv[u] = use ? vv[u] : T(0);
+            jj[u] = use ? (jj[u] & rmask) * KT : 0;
+        }
+        const bool longrow = valid && e - a > NP;
+        consume(rinv);
+#pragma unroll
+        for (int r = 0; r < KT; ++r) consume(bv[r]);
+        // ---- 2. wait for every group of the earlier levels
+        bool ok = true;
+        {
+            WaitClock clk;
+            int done;
+            while ((done = ld_relaxed_cta_smem(sm.ctr + 1)) < G.wait) {
+                if (G.wait - done > nwarps) __nanosleep(200);
+                if (clk.expired(w)) { ok = false; break; }
+            }
+            fence_acq_rel_cta();
+        }
+        if (!__all_sync(SPT_FULL_MASK, ok)) return false;
+        // ---- 3. dependencies: ring, then global memory, then long rows' tails
+#pragma unroll
+        for (int u = 0; u < NP; ++u) axpy_vec<T, KT>(vv[u], ring0 + jj[u], acc);
+        if (__any_sync(SPT_FULL_MASK, any_glob)) {
+            for (int p = a; any_glob && p < e && p < a + NP; ++p) {
+                const int j = RV<T, TR>::col(A, p);
+                if (pos_of(j) < lo) {
+                    const T v = RV<T, TR>::val(A, p);
+                    const T *xx = R.x + (int64_t)j * R.ld;
+#pragma unroll
+                    for (int r = 0; r < KT; ++r)
+                        if (r < kt) acc[r] += v * xx[r];
+                }
+            }
+        }
+        if (__any_sync(SPT_FULL_MASK, longrow)) {
+            for (int p = a + NP; longrow && p < e; ++p) {
+                const int j = RV<T, TR>::col(A, p);
+                const int pj = pos_of(j);
+                const T v = RV<T, TR>::val(A, p);
+                if (pj >= lo) {
+                    axpy_vec<T, KT>(v, ring0 + (pj & rmask) * KT, acc);
+                } else {
+                    const T *xx = R.x + (int64_t)j * R.ld;
+#pragma unroll
+                    for (int r = 0; r < KT; ++r)
+                        if (r < kt) acc[r] += v * xx[r];
+                }
+            }
+        }
+        T t[KT];
+#pragma unroll
+        for (int r = 0; r < KT; ++r) t[r] = (bv[r] - acc[r]) * rinv;
+        // ---- 4. publish: ring slot and global copy, then (release) the count
+        if (valid) {
+            store_vec<T, KT>(const_cast<T *>(sm.xr) + (pos & rmask) * KT, t);
+            T *xx = R.x + (int64_t)i * R.ld;
+#pragma unroll
+            for (int r = 0; r < KT; ++r)
+                if (r < kt) xx[r] = t[r];
+        }
+        const bool hold = __any_sync(SPT_FULL_MASK, valid && i == withhold);
+        __syncwarp();
+        if (lane == 0 && !hold) {
+            fence_acq_rel_cta();
+            atomicAdd(sm.ctr + 1, 1);
+        }
+    }
+    return true;
+}
+
 // Entry used by the kernels: `nwarps` warps of the block work on the system
 // (the others return at once); one lane per row uses the column sweep,
 // two-phase (TWO) or single-phase.

@@ -119,6 +119,15 @@ constexpr size_t kBatchSmemGrow = 48 * 1024;
 constexpr size_t kBlockSmemBudget = 200 * 1024;
 
 // ---------------------------------------------------------------- batched
+// Up to 32 rows of one level, in the processing order of one direction
+// (forward: level order; transpose: its reverse).  Positions [base,
+// base+cnt) of that order; the group's level ends at position lend; wait =
+// number of groups of the levels before it in that order (the group may
+// start once that many groups are complete).
+struct LevelGroup {
+    int32_t base, cnt, lend, wait;
+};
+
 // Per-matrix descriptor of a batched plan (device resident).
 struct BatchMat {
     int32_t n;
@@ -134,7 +143,17 @@ struct BatchMat {
     int64_t rhs_off;   // element offset of the [n x k] block in packed buffers
     int64_t vals_off;  // element offset of the nnz values in packed gradients
     int64_t row_off;   // first global row of the matrix
+    // level-ordered schedule (set once a direction of the system uses it):
+    // rows in level order, the inverse permutation, and per direction the
+    // row groups of that order (transpose: levels from the last to the first)
+    const int32_t *perm, *iperm;
+    const LevelGroup *lgroups[2];
+    int32_t nlgroups[2];
 };
+
+// Schedules of a batched work item.
+constexpr int32_t kSchedInOrder = 0;  // row groups in row order, completed one after another
+constexpr int32_t kSchedLevel = 1;    // row groups of one level, levels one after another
 
 // Work item of a batched solve: the columns [r0, r0+kt) of one system's
 // right-hand sides (the columns are independent problems, so a system with
@@ -148,6 +167,7 @@ struct BatchItem {
     int32_t kc;       // ring row groups (block mode)
     int32_t P;        // throttle distance in row groups
     int32_t nw;       // active warps of the thread block
+    int32_t sched;    // kSchedInOrder or kSchedLevel
 };
 
 // 32 consecutive rows (fewer at a system's end) of one system of a batch.
@@ -189,5 +209,7 @@ template <class T>
 cudaError_t batch_tt_apply(const BatchMat *mats, const RowChunk *tchunks, int64_t ntchunks,
                            int64_t total_rhs, const T *gbp, T *gb, cudaStream_t s);
 int batch_grid(size_t smem, const DeviceInfo &di);
+// iperm[perm[q]] = q for q < n.
+cudaError_t inverse_perm(const int32_t *perm, int32_t *iperm, int32_t n, cudaStream_t s);
 
 }  // namespace spt

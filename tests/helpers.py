@@ -27,6 +27,16 @@ def wide_level(n, seed=0):
     return S._assemble(n, k, cols, rng)
 
 
+def two_wide_levels(m, seed=0):
+    """m independent rows, then m rows that each depend on 3 random rows of
+    the first m: two levels of m rows (wider than a shared-memory ring when
+    m is large)."""
+    rng = np.random.default_rng(seed)
+    k = np.concatenate([np.zeros(m, np.int64), np.full(m, 3, np.int64)])
+    cols = np.concatenate([np.sort(rng.choice(m, 3, replace=False)) for _ in range(m)])
+    return S._assemble(2 * m, k, cols, rng)
+
+
 def long_row(n=2000, width=512, seed=0):
     """Random band matrix whose last row has `width` off-diagonals."""
     A = S.band_random(n - 1, 40, 0, 6, seed=seed)

@@ -9,8 +9,9 @@ from paper_2609_40159_gb300 import autotune
 
 
 class _Mat:
-    def __init__(self, n, nnz):
+    def __init__(self, n, nnz, nlevels=None):
         self.n, self.nnz = n, nnz
+        self.nlevels = nlevels if nlevels is not None else n // 2
 
 
 class _FakeBatch:
@@ -18,7 +19,11 @@ class _FakeBatch:
         self.mats, self.nrhs = mats, nrhs
         self.rpw = [0] * len(mats)
         self.tile = [8] * len(mats)
+        self.sched = ["inorder"] * len(mats)
         self.calls = 0
+
+    def set_schedule(self, schedule, direction="both"):
+        self.sched = [v if v else self.sched[m] for m, v in enumerate(schedule)]
 
     def set_geometry(self, rows_per_warp=None, rhs_tile=None, direction="both"):
         self.direction = direction
@@ -39,7 +44,10 @@ class _FakeBatch:
         cost = []
         for m, A in enumerate(self.mats):
             t, r = self.tile[m], self.rpw[m] or 32
-            per_item = A.n * (1 + 0.3 * t) * (1.0 if r == 32 else 1.5)
+            if self.sched[m] == "level":   # a chain of levels instead of rows
+                per_item = 12 * A.nlevels * (1 + 0.3 * t)
+            else:
+                per_item = A.n * (1 + 0.3 * t) * (1.0 if r == 32 else 1.5)
             items = -(-self.nrhs[m] // t)
             cost.append((per_item, items))
         longest = max(c for c, _ in cost)
@@ -95,3 +103,16 @@ def test_tune_batch_direction_sets_that_direction_only(monkeypatch):
     import pytest
     with pytest.raises(ValueError):
         autotune.tune_batch(fake, torch.zeros(4), direction="sideways")
+
+
+def test_tune_batch_picks_the_level_schedule_where_it_pays(monkeypatch):
+    """Systems whose levels are wide (n / levels >> 12 in the model) are
+    moved to the level-ordered schedule, the others stay in row order."""
+    mats = ([_Mat(40_000, 400_000, nlevels=400) for _ in range(4)] +
+            [_Mat(40_000, 400_000, nlevels=30_000) for _ in range(4)])
+    fake = _FakeBatch(mats, [1] * 4 + [30] * 4)   # different classes (nrhs)
+    monkeypatch.setattr(autotune, "time_call", lambda fn, reps=3: (fn(), fake.model_ms())[1])
+    res = autotune.tune_batch(fake, torch.zeros(4), reps=1)
+    assert fake.sched[:4] == ["level"] * 4
+    assert fake.sched[4:] == ["inorder"] * 4
+    assert {v["schedule"] for v in res["choice"].values()} == {"level", "inorder"}

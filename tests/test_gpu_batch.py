@@ -272,3 +272,88 @@ def test_batch_bounded_wait_reports_timeout(trans):
     ref = oracle.solve_transpose if trans else oracle.solve
     for m, A in enumerate(systems):
         assert relerr(plan.unpack(x, m).cpu().numpy(), ref(A, bs[m])) <= TOL[np.float64], m
+
+@pytest.mark.parametrize("dt", [np.float32, np.float64], ids=["f32", "f64"])
+def test_batch_level_schedule(dt):
+    """The level-ordered schedule (the groups of one level at the same time,
+    levels one after another; transpose: levels last to first) on every
+    system, then on every other system with a different tile per system:
+    forward solve, transpose solve, T^T and g_vals vs the oracle, rewritten
+    systems included; then back to the in-order schedule."""
+    items = S.batch_spec(nmat=40, seed=13, n_lo=300, n_hi=20_000, w_lo=8, w_hi=1024, dtype=dt)
+    P, plan, b, refs = _build(items, dt)
+    nm = len(items)
+    for sched, tiles in (("level", None),
+                         (["level", "inorder"] * (nm // 2), [(1, 2, 4, 8)[m % 4] for m in range(nm)]),
+                         ("inorder", 4)):
+        plan.set_schedule(sched)
+        if tiles is not None:
+            plan.set_geometry(rhs_tile=tiles)
+        x = plan.solve(b)
+        w = torch.randn_like(b)
+        gbp = plan.solve_transpose(w)
+        gb = plan.tt_apply(gbp)
+        gv = plan.grad_vals(gbp, x)
+        assert P.handle().status() == 0
+        for m, it in enumerate(items):
+            _check_system(plan, m, it, refs[m], x, w, gb, gv, dt)
+    with pytest.raises(P.SpTRSVError):
+        P._lib.check(P._lib.lib().sptrsv_batch_plan_set_schedule(
+            plan.p, 0, (__import__("ctypes").c_int32 * nm)(*([3] * nm))))
+
+
+def test_batch_level_schedule_edge_cases():
+    """Level-ordered schedule on degenerate level structures: levels wider
+    than the shared-memory ring (dependencies read from global memory), one
+    level of 5,000 rows, 1-row levels (a chain), n = 1, row counts around
+    the 32-row group, a long row, a wide band; forward and transpose, tiles
+    1 and 8, each direction scheduled on its own."""
+    import paper_2609_40159_gb300 as P
+    from helpers import long_row, two_wide_levels
+    systems = [two_wide_levels(6000, seed=1), S.diagonal(5000, seed=2), S.chain(1000, seed=3),
+               S.band_random(1, 4, 0, 4, seed=4), S.band_random(31, 8, 0, 6, seed=5),
+               S.band_random(33, 40, 1, 20, seed=6), long_row(), S.band_random(4097, 700, 10, 40, seed=7),
+               S.lap2d(70)]
+    nrhs = [3, 1, 32, 1, 5, 32, 2, 9, 4]
+    rng = np.random.default_rng(8)
+    mats = [P.Matrix.from_host(A) for A in systems]
+    plan = P.BatchPlan(mats, None, nrhs, transpose=True)
+    bs = [rng.uniform(-1, 1, (A.n, k)) for A, k in zip(systems, nrhs)]
+    b = torch.cat([torch.as_tensor(v).reshape(-1) for v in bs]).cuda()
+    plan.set_schedule("level", direction="forward")
+    plan.set_schedule("level", direction="transpose")
+    for tile in (1, 8):
+        plan.set_geometry(rhs_tile=tile)
+        x = plan.solve(b)
+        gb = plan.solve_transpose(b)
+        assert P.handle().status() == 0
+        for m, A in enumerate(systems):
+            xr, gr = oracle.solve(A, bs[m]), oracle.solve_transpose(A, bs[m])
+            assert relerr(plan.unpack(x, m).cpu().numpy(), xr) <= TOL[np.float64], (tile, m)
+            assert relerr(plan.unpack(gb, m).cpu().numpy(), gr) <= TOL[np.float64], (tile, m)
+
+
+@pytest.mark.parametrize("trans", [False, True], ids=["fwd", "transpose"])
+def test_batch_level_schedule_bounded_wait(trans):
+    """A withheld row under the level-ordered schedule: the groups of the
+    later levels give up after the wait limit with SPTRSV_ETIMEOUT, and the
+    next solve is right again."""
+    import paper_2609_40159_gb300 as P
+    systems = [S.lap2d(40), S.band_random(3000, 64, 1, 6, seed=2)]
+    mats = [P.Matrix.from_host(A) for A in systems]
+    plan = P.BatchPlan(mats, None, [1, 2], transpose=True, wait_limit_us=20_000)
+    plan.set_schedule("level")
+    rng = np.random.default_rng(3)
+    bs = [rng.uniform(-1, 1, (A.n, k)) for A, k in zip(systems, [1, 2])]
+    b = torch.cat([torch.as_tensor(v).reshape(-1) for v in bs]).cuda()
+    h = P.handle()
+    run = plan.solve_transpose if trans else plan.solve
+    plan.withhold(1, 1500)
+    run(b)
+    assert h.status() == P._lib.SPTRSV_ETIMEOUT
+    plan.withhold(-1, 0)
+    x = run(b)
+    assert h.status() == 0
+    ref = oracle.solve_transpose if trans else oracle.solve
+    for m, A in enumerate(systems):
+        assert relerr(plan.unpack(x, m).cpu().numpy(), ref(A, bs[m])) <= TOL[np.float64], m
