@@ -418,81 +418,45 @@ def main():
                                "probe": "chain of 131,072 rows (1 row per level), FP32, 1 RHS, "
                                         "batched kernel, CUDA events, median of 5"}
 
-    # end to end through the C ABI with host buffers: every step copies its
-    # inputs from pinned host memory and its results back; two buffer sets
-    # let step t's copies overlap the compute of step t-1 (compute stays in
-    # order on one stream, since the plan's control block is shared)
+    # end to end through the C ABI with host buffers (sptrsv_batch_step_host):
+    # every step copies its inputs from pinned host memory and its results
+    # back; the library alternates two device buffer sets, so that one
+    # step's copies overlap the neighbouring steps' solves.  Host wall clock
+    # around Ke enqueued steps and the final wait.
     e2e = None
     if not args.ncu:
         pin = lambda t: torch.empty(t.numel(), dtype=t.dtype, pin_memory=True)
         hb, hw, hx, hgb, hgv = pin(b), pin(w), pin(x), pin(gb), pin(gv)
         hb.copy_(b.cpu())
         hw.copy_(w.cpu())
-        b2, w2 = b.clone(), w.clone()
-        x2, gbp2, gb2, gv2 = torch.empty_like(x), torch.empty_like(gbp), torch.empty_like(gb), torch.empty_like(gv)
-        with torch.cuda.stream(s):
-            gplan.solve(b2, out=x2)  # warm the second set once before capture
-            torch.cuda.synchronize()
-            g2 = [torch.cuda.CUDAGraph() for _ in range(3)]
-            with torch.cuda.graph(g2[0], stream=s):
-                gplan.solve(b2, out=x2)
-            with torch.cuda.graph(g2[1], stream=s):
-                gplan.solve_transpose(w2, out=gbp2)
-            with torch.cuda.graph(g2[2], stream=s):
-                gplan.tt_apply(gbp2, out=gb2)
-                gplan.grad_vals(gbp2, x2, out=gv2)
-        sets = [dict(b=b, w=w, x=x, gb=gb, gv=gv, graphs=[g_f, g_t, g_r]),
-                dict(b=b2, w=w2, x=x2, gb=gb2, gv=gv2, graphs=g2)]
-        sh, sd = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
-        torch.cuda.synchronize()
+        gplan.step_host(hb, hw, hx, hgb, hgv)  # the first call allocates the device sets
+        gplan.step_wait()
         Ke = max(4, min(K, 10))
-        ev = lambda: torch.cuda.Event(enable_timing=False)
-        comp_done = [None, None]
-        d2h_done = [None, None]
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(sh)
-        for t in range(Ke):
-            bs = sets[t % 2]
-            with torch.cuda.stream(sh):
-                if comp_done[t % 2] is not None:
-                    sh.wait_event(comp_done[t % 2])  # step t-2 no longer reads this set
-                bs["b"].copy_(hb, non_blocking=True)
-                bs["w"].copy_(hw, non_blocking=True)
-                h2d = ev()
-                h2d.record(sh)
-            with torch.cuda.stream(s):
-                s.wait_event(h2d)
-                if d2h_done[t % 2] is not None:
-                    s.wait_event(d2h_done[t % 2])  # step t-2's results are copied out
-                for g in bs["graphs"]:
-                    g.replay()
-                comp_done[t % 2] = ev()
-                comp_done[t % 2].record(s)
-            with torch.cuda.stream(sd):
-                sd.wait_event(comp_done[t % 2])
-                hx.copy_(bs["x"], non_blocking=True)
-                hgb.copy_(bs["gb"], non_blocking=True)
-                hgv.copy_(bs["gv"], non_blocking=True)
-                d2h_done[t % 2] = ev()
-                d2h_done[t % 2].record(sd)
-        with torch.cuda.stream(sd):
-            e1.record(sd)
         torch.cuda.synchronize()
-        e2e_ms = e0.elapsed_time(e1) / Ke
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(Ke):
+            gplan.step_host(hb, hw, hx, hgb, hgv)
+        gplan.step_wait()
+        e2e_ms = (time.perf_counter() - t0) * 1e3 / Ke
         if dist:
             tm = torch.tensor([e2e_ms], device=dev)
             dist.all_reduce(tm, op=dist.ReduceOp.MAX)  # the slowest rank bounds the job
             e2e_ms = float(tm.item())
         if P.handle().status() != 0:
             raise RuntimeError("device status after the end-to-end run")
+        # the host results are the device path's (same kernels, same inputs)
+        if not (torch.equal(hx[:1 << 20], x[:1 << 20].cpu()) and torch.equal(hgv[-(1 << 20):], gv[-(1 << 20):].cpu())):
+            raise RuntimeError("end-to-end results differ from the device path")
         e2e = {"value": world * step_bytes / (e2e_ms * 1e-3) / 1e9, "unit": "GB/s",
                "ms_per_step": e2e_ms, "steps": Ke,
-               "how": "per step: H2D of b and w from pinned host memory, fwd + adjoint graphs, "
-                      "D2H of x, g_b and g_vals; two device buffer sets so that copies overlap "
-                      "the neighbouring steps' compute",
+               "how": "sptrsv_batch_step_host per step (H2D of b and w from pinned host memory, fwd + "
+                      "transpose solve, T^T, value gradient, D2H of x, g_b and g_vals; two device buffer "
+                      "sets inside the library so that copies overlap the neighbouring steps' solves), "
+                      "sptrsv_batch_step_wait at the end; host wall clock",
                "h2d_bytes_per_step": int(hb.numel() * 4 + hw.numel() * 4),
                "d2h_bytes_per_step": int(hx.numel() * 4 + hgb.numel() * 4 + hgv.numel() * 4)}
-        del sets, b2, w2, x2, gbp2, gb2, gv2, g2
 
     # one host-side gather of every rank's report (no collective in the data path)
     from paper_2609_40159_gb300 import shard

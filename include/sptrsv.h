@@ -307,6 +307,30 @@ sptrsv_status sptrsv_batch_grad_vals(sptrsv_plan plan, const void *gb, const voi
                                      void *gvals);
 sptrsv_status sptrsv_batch_tt_apply(sptrsv_plan plan, const void *gbp, void *gb);
 
+/* One forward + adjoint step of a batch whose data live in HOST memory (the
+ * call of an application that keeps its right-hand sides on the host):
+ *   b      host, packed right-hand sides (rhs_offset[nmat] elements of the
+ *          plan's dtype);
+ *   w      host, packed dL/dx of the same layout;
+ *   x      host out: x = L^{-1} b (rewritten systems: L'^{-1} (b + T b));
+ *   gb     host out: dL/db = L^{-T} w (rewritten: g + T^T g, g = L'^{-T} w);
+ *   gvals  host out: dL/dvals on each system's pattern (vals_offset[nmat]
+ *          elements; rewritten systems: on L').
+ * Enqueues the copies of b and w to the device, the four batched calls
+ * above and the copies back, and returns without waiting.  Consecutive
+ * steps alternate between two plan-owned device buffer sets, so that one
+ * step's copies overlap the neighbouring steps' solves.  The host buffers
+ * must stay valid and unchanged until sptrsv_batch_step_wait returns;
+ * page-locked host memory lets the copies run asynchronously.  The first
+ * call allocates the two sets (2 x (5 rhs_offset[nmat] + vals_offset[nmat])
+ * elements) and two copy streams; the solves run on the handle's stream.
+ * Needs a plan built with the transpose (else SPTRSV_ENOTSUP).             */
+sptrsv_status sptrsv_batch_step_host(sptrsv_plan plan, const void *b, const void *w, void *x, void *gb,
+                                     void *gvals);
+/* Waits for every step enqueued by sptrsv_batch_step_host and returns the
+ * handle's device status (SPTRSV_OK, or e.g. SPTRSV_ETIMEOUT).             */
+sptrsv_status sptrsv_batch_step_wait(sptrsv_plan plan);
+
 /* --------------------------------------------------- allocation-free solve */
 /* The paper has no counterpart of this entry point; it exists for callers
  * that cannot allocate device memory when they solve (an application whose

@@ -111,6 +111,8 @@ _SIGS = {
     "sptrsv_batch_solve_transpose": [sptrsv_plan, _P, _P],
     "sptrsv_batch_grad_vals": [sptrsv_plan, _P, _P, _P],
     "sptrsv_batch_tt_apply": [sptrsv_plan, _P, _P],
+    "sptrsv_batch_step_host": [sptrsv_plan, _P, _P, _P, _P, _P],
+    "sptrsv_batch_step_wait": [sptrsv_plan],
     "sptrsv_debug_withhold_row": [sptrsv_plan, _I32],
     "sptrsv_debug_withhold_level": [sptrsv_handle, _I32, _I64],
     "sptrsv_batch_trace": [sptrsv_plan, _PI64],

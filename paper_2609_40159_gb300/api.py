@@ -434,6 +434,22 @@ class BatchPlan:
         L.check(L.lib().sptrsv_batch_tt_apply(self.p, _ptr(gbp), _ptr(gb)), "sptrsv_batch_tt_apply")
         return gb
 
+    def step_host(self, b, w, x, gb, gvals):
+        """One forward + adjoint step from HOST buffers (CPU tensors of the
+        plan's dtype, contiguous; page-locked for overlapped copies): x =
+        solve(b), gb = dL/db and gvals = dL/dvals for dL/dx = w.  Returns
+        without waiting; the buffers must stay untouched until step_wait()."""
+        for t, size in ((b, self.total_rhs), (w, self.total_rhs), (x, self.total_rhs), (gb, self.total_rhs),
+                        (gvals, self.total_nnz)):
+            if t.dtype != self.dtype or t.is_cuda or t.numel() != size or not t.is_contiguous():
+                raise ValueError(f"host buffer must be a contiguous CPU {self.dtype} tensor of {size} elements")
+        L.check(L.lib().sptrsv_batch_step_host(self.p, _ptr(b), _ptr(w), _ptr(x), _ptr(gb), _ptr(gvals)),
+                "sptrsv_batch_step_host")
+
+    def step_wait(self):
+        """Waits for the steps enqueued by step_host; raises on a device error."""
+        L.check(L.lib().sptrsv_batch_step_wait(self.p), "sptrsv_batch_step_wait")
+
     def withhold(self, m: int, i: int):
         """Test hook of the bounded waits: row i of system m is never
         published by the next solves (m = -1 clears it)."""

@@ -100,6 +100,9 @@ struct PlanMat {
     int32_t *d_cp = nullptr, *d_crow = nullptr, *d_tmap = nullptr;
     void *d_cv = nullptr;  // L's values in CSC order (transpose solves)
     uint32_t *d_tmask = nullptr;
+    // CSC of T (the adjoint's T^T gathers by column), its column mask
+    int32_t *d_tcp = nullptr, *d_trow = nullptr, *d_ttmap = nullptr;
+    uint32_t *d_tcmask = nullptr;
     // level-ordered batched schedule (built when first used): inverse of
     // d_perm, row groups of each direction
     int32_t *d_iperm = nullptr;
@@ -150,6 +153,16 @@ struct sptrsv_plan_st {
     int64_t n_fchunks = 0;
     void *d_bt = nullptr;           // b + T b of the rewritten systems (packed like b)
     long long *d_trace = nullptr;  // per work item: start ns, end ns, SM of the last batch solve
+    // steps from host buffers (sptrsv_batch_step_host): two device buffer
+    // sets used alternately, a stream for the copies in and one for the
+    // copies out (the solves run on the handle's stream)
+    struct HostSet {
+        void *b = nullptr, *w = nullptr, *x = nullptr, *gbp = nullptr, *gb = nullptr, *gv = nullptr;
+        cudaEvent_t h2d = nullptr, comp = nullptr, d2h = nullptr;
+        bool used = false;
+    } hset[2];
+    cudaStream_t s_h2d = nullptr, s_d2h = nullptr;
+    int64_t nsteps = 0;
 
     template <class P> cudaError_t alloc(P **p, size_t bytes)
     {
@@ -334,6 +347,7 @@ template <class T> Sys<T> sys_of(const PlanMat &M)
     A.tci = M.hasT ? M.T.col_idx : nullptr;
     A.tv = M.hasT ? (const T *)M.T.vals : nullptr;
     A.tmask = M.hasT ? M.d_tmask : nullptr;
+    A.tcp = M.d_tcp; A.trow = M.d_trow; A.ttmap = M.d_ttmap;
     return A;
 }
 
@@ -367,8 +381,18 @@ sptrsv_status prepare_mat(sptrsv_plan p, PlanMat &M, const sptrsv_csr &L, const 
         if (e != cudaSuccess) return from_cuda(e);
     }
     if (M.hasT) {
+        const size_t tnz = (size_t)(M.T.nnz > 0 ? M.T.nnz : 1);
         e = p->alloc(&M.d_tmask, sizeof(uint32_t) * ((nn + 31) / 32));
         if (e == cudaSuccess) e = build_tmask(M.T.row_ptr, n, M.d_tmask, s);
+        if (e == cudaSuccess) e = p->alloc(&M.d_tcp, sizeof(int32_t) * (nn + 1));
+        if (e == cudaSuccess) e = p->alloc(&M.d_trow, sizeof(int32_t) * tnz);
+        if (e == cudaSuccess) e = p->alloc(&M.d_ttmap, sizeof(int32_t) * tnz);
+        if (e == cudaSuccess) e = p->alloc(&M.d_tcmask, sizeof(uint32_t) * ((nn + 31) / 32));
+        if (e == cudaSuccess)
+            e = M.T.nnz > 0 ? build_csc(M.T.row_ptr, M.T.col_idx, n, M.T.nnz, M.d_tcp, M.d_trow, M.d_ttmap, s)
+                            : cudaMemsetAsync(M.d_tcp, 0, sizeof(int32_t) * (nn + 1), s);
+        if (e == cudaSuccess) e = build_tmask(M.d_tcp, n, M.d_tcmask, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return from_cuda(e);
     }
     if (want_csc) {
@@ -626,6 +650,14 @@ extern "C" sptrsv_status sptrsv_plan_destroy(sptrsv_plan p)
 {
     if (!p) return SPTRSV_EINVAL;
     if (p->h) cudaStreamSynchronize(p->h->stream);
+    for (auto &S : p->hset)
+        for (cudaEvent_t ev : {S.h2d, S.comp, S.d2h})
+            if (ev) cudaEventDestroy(ev);
+    for (cudaStream_t st : {p->s_h2d, p->s_d2h})
+        if (st) {
+            cudaStreamSynchronize(st);
+            cudaStreamDestroy(st);
+        }
     for (void *q : p->owned) cudaFree(q);
     delete p;
     return SPTRSV_OK;
@@ -949,6 +981,7 @@ extern "C" sptrsv_status sptrsv_batch_plan_create(sptrsv_handle h, int32_t nmat,
         B.tci = M.hasT ? M.T.col_idx : nullptr;
         B.tv = M.hasT ? M.T.vals : nullptr;
         B.tmask = M.hasT ? M.d_tmask : nullptr;
+        B.tcp = M.d_tcp; B.trow = M.d_trow; B.ttmap = M.d_ttmap;
         B.rhs_off = p->rhs_off[m];
         B.vals_off = p->vals_off[m];
         B.row_off = p->row_off[m];
@@ -974,7 +1007,7 @@ extern "C" sptrsv_status sptrsv_batch_plan_create(sptrsv_handle h, int32_t nmat,
     if (e != cudaSuccess) { sptrsv_plan_destroy(p); return from_cuda(e); }
     {
         // chunk tables of the elementwise adjoint kernels: every 32-row chunk,
-        // and the chunks whose T-row mask word is non-zero
+        // and the chunks whose T-column mask word is non-zero
         std::vector<RowChunk> g, t, f;
         std::vector<uint32_t> mask;
         e = cudaStreamSynchronize(p->h->stream);  // T-row masks are built on the handle's stream
@@ -985,7 +1018,7 @@ extern "C" sptrsv_status sptrsv_batch_plan_create(sptrsv_handle h, int32_t nmat,
             if (!M.hasT || nw == 0) continue;
             for (int32_t c = 0; c < nw; ++c) f.push_back(RowChunk{m, 32 * c});
             mask.resize((size_t)nw);
-            e = cudaMemcpy(mask.data(), M.d_tmask, sizeof(uint32_t) * nw, cudaMemcpyDeviceToHost);
+            e = cudaMemcpy(mask.data(), M.d_tcmask, sizeof(uint32_t) * nw, cudaMemcpyDeviceToHost);
             for (int32_t c = 0; c < nw && e == cudaSuccess; ++c)
                 if (mask[c]) t.push_back(RowChunk{m, 32 * c});
         }
@@ -1157,4 +1190,82 @@ extern "C" sptrsv_status sptrsv_batch_tt_apply(sptrsv_plan p, const void *gbp, v
         e = batch_tt_apply<float>(p->d_mats, p->d_tchunks, p->n_tchunks, p->rhs_off[nmat], (const float *)gbp,
                                   (float *)gb, p->h->stream);
     return from_cuda(e);
+}
+
+// ------------------------------------------------------ steps from host buffers
+namespace {
+sptrsv_status ensure_host_sets(sptrsv_plan p)
+{
+    if (p->s_h2d) return SPTRSV_OK;
+    const int32_t nmat = (int32_t)p->mats.size();
+    const size_t w = p->dtype == SPTRSV_F64 ? 8 : 4;
+    const size_t rhs = w * (size_t)std::max<int64_t>(p->rhs_off[nmat], 1);
+    const size_t nz = w * (size_t)std::max<int64_t>(p->vals_off[nmat], 1);
+    cudaError_t e = cudaSuccess;
+    for (auto &S : p->hset) {
+        for (void **q : {&S.b, &S.w, &S.x, &S.gbp, &S.gb})
+            if (e == cudaSuccess) e = p->alloc(q, rhs);
+        if (e == cudaSuccess) e = p->alloc(&S.gv, nz);
+        for (cudaEvent_t *ev : {&S.h2d, &S.comp, &S.d2h})
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->s_h2d, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->s_d2h, cudaStreamNonBlocking);
+    return from_cuda(e);
+}
+}  // namespace
+
+extern "C" sptrsv_status sptrsv_batch_step_host(sptrsv_plan p, const void *b, const void *w, void *x, void *gb,
+                                                void *gvals)
+{
+    Range range("sptrsv_batch_step_host");
+    if (!p || !p->batched || !b || !w || !x || !gb || !gvals) return SPTRSV_EINVAL;
+    if (!p->have_csc) return SPTRSV_ENOTSUP;
+    const int32_t nmat = (int32_t)p->mats.size();
+    if (nmat == 0 || p->rhs_off[nmat] == 0) return SPTRSV_OK;
+    sptrsv_status st = ensure_host_sets(p);
+    if (st != SPTRSV_OK) return st;
+    const size_t wb = p->dtype == SPTRSV_F64 ? 8 : 4;
+    const size_t rhs = wb * (size_t)p->rhs_off[nmat];
+    const size_t nz = wb * (size_t)p->vals_off[nmat];
+    sptrsv_plan_st::HostSet &S = p->hset[p->nsteps & 1];
+    cudaStream_t hs = p->h->stream;
+    // copies in, once the previous step on this set no longer reads b and w
+    cudaError_t e = S.used ? cudaStreamWaitEvent(p->s_h2d, S.comp, 0) : cudaSuccess;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(S.b, b, rhs, cudaMemcpyHostToDevice, p->s_h2d);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(S.w, w, rhs, cudaMemcpyHostToDevice, p->s_h2d);
+    if (e == cudaSuccess) e = cudaEventRecord(S.h2d, p->s_h2d);
+    // the step, once its inputs are in and the previous results of the set are out
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(hs, S.h2d, 0);
+    if (e == cudaSuccess && S.used) e = cudaStreamWaitEvent(hs, S.d2h, 0);
+    if (e != cudaSuccess) return from_cuda(e);
+    st = sptrsv_batch_solve(p, S.b, S.x);
+    if (st == SPTRSV_OK) st = sptrsv_batch_solve_transpose(p, S.w, S.gbp);
+    if (st == SPTRSV_OK) st = sptrsv_batch_tt_apply(p, S.gbp, S.gb);
+    if (st == SPTRSV_OK) st = sptrsv_batch_grad_vals(p, S.gbp, S.x, S.gv);
+    if (st != SPTRSV_OK) return st;
+    e = cudaEventRecord(S.comp, hs);
+    // copies out
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(p->s_d2h, S.comp, 0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(x, S.x, rhs, cudaMemcpyDeviceToHost, p->s_d2h);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(gb, S.gb, rhs, cudaMemcpyDeviceToHost, p->s_d2h);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(gvals, S.gv, nz, cudaMemcpyDeviceToHost, p->s_d2h);
+    if (e == cudaSuccess) e = cudaEventRecord(S.d2h, p->s_d2h);
+    S.used = true;
+    ++p->nsteps;
+    return from_cuda(e);
+}
+
+extern "C" sptrsv_status sptrsv_batch_step_wait(sptrsv_plan p)
+{
+    Range range("sptrsv_batch_step_wait");
+    if (!p || !p->batched) return SPTRSV_EINVAL;
+    cudaError_t e = cudaStreamSynchronize(p->h->stream);
+    if (e == cudaSuccess && p->s_h2d) e = cudaStreamSynchronize(p->s_h2d);
+    if (e == cudaSuccess && p->s_d2h) e = cudaStreamSynchronize(p->s_d2h);
+    if (e != cudaSuccess) return from_cuda(e);
+    int status = 0;
+    e = cudaMemcpy(&status, p->h->d_status, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return from_cuda(e);
+    return (sptrsv_status)status;
 }

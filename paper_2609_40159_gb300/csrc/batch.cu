@@ -21,6 +21,7 @@ __device__ __forceinline__ Sys<T> sys_of(const BatchMat &M)
     A.rp = M.rp; A.ci = M.ci; A.v = (const T *)M.v;
     A.cp = M.cp; A.crow = M.crow; A.tmap = M.tmap; A.cv = (const T *)M.cv;
     A.trp = M.trp; A.tci = M.tci; A.tv = (const T *)M.tv; A.tmask = M.tmask;
+    A.tcp = M.tcp; A.trow = M.trow; A.ttmap = M.ttmap;
     return A;
 }
 
@@ -153,8 +154,11 @@ __global__ void k_batch_grad(const BatchMat *__restrict__ mats, const RowChunk *
     }
 }
 
-// g_b += T^T g_b' for the rewritten rows: one warp per 32-row chunk that
-// holds at least one row of T (its T-row mask word is non-zero).
+// g_b = g_b' + T^T g_b' on the rows of the rewritten systems that are
+// columns of T: one warp per 32-row chunk holding at least one such column,
+// one lane per row; each lane gathers its column of T (CSC, rows ascending)
+// and writes its row of g_b once -- no atomics, so the result does not
+// depend on the schedule.  The other rows of g_b are the copy of g_b'.
 template <class T>
 __global__ void k_batch_tt(const BatchMat *__restrict__ mats, const RowChunk *__restrict__ chunks,
                            int64_t nchunks, const T *__restrict__ gbp, T *gb)
@@ -165,18 +169,18 @@ __global__ void k_batch_tt(const BatchMat *__restrict__ mats, const RowChunk *__
     for (int64_t c = gw; c < nchunks; c += nw) {
         const RowChunk ch = chunks[c];
         const BatchMat &M = mats[ch.mat];
+        const int j = ch.r0 + lane;
+        if (j >= M.n) continue;
+        const int qa = ldro(M.tcp + j), qe = ldro(M.tcp + j + 1);
+        if (qa == qe) continue;
         const int k = M.k;
         const T *tv = (const T *)M.tv;
-        unsigned word = M.tmask[ch.r0 >> 5];
-        while (word) {
-            const int i = ch.r0 + __ffs(word) - 1;
-            word &= word - 1;
-            const T *gi = gbp + M.rhs_off + (int64_t)i * k;
-            for (int p = ldro(M.trp + i) + lane; p < ldro(M.trp + i + 1); p += 32) {
-                const T cv = ldro(tv + p);
-                T *gj = gb + M.rhs_off + (int64_t)ldro(M.tci + p) * k;
-                for (int q = 0; q < k; ++q) atomicAdd(gj + q, cv * gi[q]);
-            }
+        const T *g0 = gbp + M.rhs_off;
+        for (int r = 0; r < k; ++r) {
+            T acc = g0[(int64_t)j * k + r];
+            for (int q = qa; q < qe; ++q)
+                acc += ldro(tv + ldro(M.ttmap + q)) * g0[(int64_t)ldro(M.trow + q) * k + r];
+            gb[M.rhs_off + (int64_t)j * k + r] = acc;
         }
     }
 }

@@ -441,20 +441,21 @@ __global__ void k_copy_rhs(const T *src, T *dst, int64_t n, int64_t ld, int32_t 
     }
 }
 
+// gb = gbp + T^T gbp, one thread per element of gb: row j gathers column j
+// of T (CSC, rows ascending), so every element is written once, in a fixed
+// order (no atomics: the result does not depend on the schedule).
 template <class T>
-__global__ void k_tt_scatter(Sys<T> A, const T *__restrict__ gbp, T *gb, int64_t ld, int32_t k)
+__global__ void k_tt_gather(Sys<T> A, const T *__restrict__ gbp, T *__restrict__ gb, int64_t ld, int32_t k)
 {
-    const int lane = threadIdx.x & 31;
-    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t i = gw; i < A.n; i += nw) {
-        if (!has_trow(A, (int)i)) continue;
-        const int a = A.trp[i], e = A.trp[i + 1];
-        for (int p = a + lane; p < e; p += 32) {
-            const T tv = A.tv[p];
-            const int64_t j = A.tci[p];
-            for (int r = 0; r < k; ++r) atomicAdd(gb + j * ld + r, tv * gbp[i * ld + r]);
-        }
+    const int64_t total = (int64_t)A.n * k;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = t / k;
+        const int r = (int)(t - j * k);
+        T acc = gbp[j * ld + r];
+        const int qa = A.tcp[j], qe = A.tcp[j + 1];
+        for (int q = qa; q < qe; ++q) acc += A.tv[A.ttmap[q]] * gbp[(int64_t)A.trow[q] * ld + r];
+        gb[j * ld + r] = acc;
     }
 }
 
@@ -464,12 +465,10 @@ cudaError_t tt_apply(const Sys<T> &A, const T *gbp, T *gb, int64_t ld, int32_t k
     if (A.n <= 0) return cudaSuccess;
     int64_t blocks = ((int64_t)A.n * k + 255) / 256;
     if (blocks > 65535 * 4) blocks = 65535 * 4;
-    k_copy_rhs<T><<<(int)blocks, 256, 0, s>>>(gbp, gb, A.n, ld, k);
-    if (A.tmask) {
-        int64_t wb = ((int64_t)A.n + 7) / 8;
-        if (wb > 65535 * 4) wb = 65535 * 4;
-        k_tt_scatter<T><<<(int)wb, 256, 0, s>>>(A, gbp, gb, ld, k);
-    }
+    if (A.tmask && A.tcp)
+        k_tt_gather<T><<<(int)blocks, 256, 0, s>>>(A, gbp, gb, ld, k);
+    else
+        k_copy_rhs<T><<<(int)blocks, 256, 0, s>>>(gbp, gb, A.n, ld, k);
     return cudaGetLastError();
 }
 

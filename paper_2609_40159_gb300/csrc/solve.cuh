@@ -22,6 +22,9 @@ template <class T> struct Sys {
     const int32_t *tci;
     const T *tv;
     const uint32_t *tmask;  // bit i set when row i has a T row; null = no T
+    const int32_t *tcp;     // CSC of T (adjoint of b + T b): column pointers,
+    const int32_t *trow;    //   row of every CSC entry (ascending),
+    const int32_t *ttmap;   //   CSR position of every CSC entry
 };
 
 // Level schedule.
@@ -140,6 +143,7 @@ struct BatchMat {
     const int32_t *trp, *tci;
     const void *tv;
     const uint32_t *tmask;
+    const int32_t *tcp, *trow, *ttmap;  // CSC of T
     int64_t rhs_off;   // element offset of the [n x k] block in packed buffers
     int64_t vals_off;  // element offset of the nnz values in packed gradients
     int64_t row_off;   // first global row of the matrix
@@ -204,7 +208,8 @@ template <class T>
 cudaError_t batch_grad_vals(const BatchMat *mats, const RowChunk *chunks, int64_t nchunks, const T *gb,
                             const T *x, T *gv, cudaStream_t s);
 // gb = gbp + T^T gbp for every rewritten matrix (packed buffers); tchunks
-// lists the chunks that hold at least one row of T.
+// lists the chunks that hold at least one column of T (rows of gb that
+// receive a T^T term).
 template <class T>
 cudaError_t batch_tt_apply(const BatchMat *mats, const RowChunk *tchunks, int64_t ntchunks,
                            int64_t total_rhs, const T *gbp, T *gb, cudaStream_t s);

@@ -357,3 +357,36 @@ def test_batch_level_schedule_bounded_wait(trans):
     ref = oracle.solve_transpose if trans else oracle.solve
     for m, A in enumerate(systems):
         assert relerr(plan.unpack(x, m).cpu().numpy(), ref(A, bs[m])) <= TOL[np.float64], m
+
+
+def test_batch_step_from_host_buffers():
+    """sptrsv_batch_step_host: three steps in flight from pinned host
+    buffers (different inputs, the two device buffer sets alternating), then
+    one wait: x, g_b and g_vals of every step equal the oracle's, rewritten
+    systems included."""
+    dt = np.float32
+    items = S.batch_spec(nmat=16, seed=41, n_lo=300, n_hi=8000, dtype=dt)
+    P, plan, b, refs = _build(items, dt)
+    n_rhs, n_nz = plan.total_rhs, plan.total_nnz
+    gen = torch.Generator().manual_seed(5)
+    steps = []
+    for t in range(3):
+        hb = torch.empty(n_rhs, dtype=torch.float32).pin_memory()
+        hb.copy_(b.cpu() * (1.0 + t))
+        hw = torch.empty(n_rhs, dtype=torch.float32).pin_memory()
+        hw.copy_(torch.randn(n_rhs, generator=gen))
+        outs = [torch.empty(n, dtype=torch.float32).pin_memory() for n in (n_rhs, n_rhs, n_nz)]
+        plan.step_host(hb, hw, *outs)
+        steps.append((hb, hw, outs))
+    plan.step_wait()
+    assert P.handle().status() == 0
+    for t, (hb, hw, (hx, hgb, hgv)) in enumerate(steps):
+        for m, it in enumerate(items):
+            a, e = int(plan.rhs_offset[m]), int(plan.rhs_offset[m + 1])
+            bm = hb[a:e].numpy().reshape(it.A.n, it.nrhs).astype(np.float64)
+            wm = hw[a:e].numpy().reshape(it.A.n, it.nrhs).astype(np.float64)
+            x_ref, gb_ref, gv_ref = refs[m].grads(bm, wm)
+            assert relerr(hx[a:e].numpy(), x_ref) <= TOL[dt], (t, m)
+            assert relerr(hgb[a:e].numpy(), gb_ref) <= TOL[dt], (t, m)
+            va, ve = int(plan.vals_offset[m]), int(plan.vals_offset[m + 1])
+            assert relerr(hgv[va:ve].numpy(), gv_ref) <= GV_TOL[dt], (t, m)

@@ -96,6 +96,36 @@ def test_rewritten_solve_and_adjoint_identity():
         assert relerr(gb, oracle.solve_transpose(A_h, b_h)) <= 1e-12
 
 
+def test_tt_apply_is_deterministic():
+    """T^T of the adjoint is a gather over T's columns (each element of g_b
+    written once, in a fixed order): repeated applications, single-system
+    and batched, are bit-identical, and equal the oracle's."""
+    import paper_2609_40159_gb300 as P
+    A_h = S.lap2d(120)
+    an = oracle.analyze(A_h)
+    rows, tg = S.narrowest_levels_list(an["nlevels"], an["level_ptr"], an["perm"], 0.05, 8)
+    A = P.Matrix.from_host(A_h)
+    Lp, T = P.rewrite(A, P.analyze(A).lev, rows, tg)
+    assert T.nnz > 0
+    Lp_o, T_o = oracle.rewrite(A_h, an["lev"], rows, tg)
+    g_h = S.rhs(A_h.n, 5, seed=7)
+    g = torch.as_tensor(g_h).cuda()
+    ref = oracle.tt_apply(T_o, g_h)
+    plan = P.Plan(Lp, T, transpose=True)
+    first = plan.tt_apply(g)
+    for _ in range(3):
+        assert torch.equal(plan.tt_apply(g), first)
+    assert relerr(first.cpu().numpy(), ref) <= 1e-12
+    bp = P.BatchPlan([Lp, Lp], [T, T], [5, 5], transpose=True)
+    gg = torch.cat([g.reshape(-1), g.reshape(-1)])
+    bfirst = bp.tt_apply(gg)
+    for _ in range(3):
+        assert torch.equal(bp.tt_apply(gg), bfirst)
+    for m in range(2):
+        assert relerr(bp.unpack(bfirst, m).cpu().numpy(), ref) <= 1e-12
+    assert P.handle().status() == 0
+
+
 def test_autograd_finite_differences_lap3d_block():
     import paper_2609_40159_gb300 as P
     A_h = S.leading_block(S.lap3d(128), 4096)
