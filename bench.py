@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--nmat", type=int, default=512)
+    ap.add_argument("--split", action="store_true",
+                    help="split ONE batch over the ranks (shard.partition, strong scaling) instead of "
+                         "one batch per rank (weak scaling)")
     ap.add_argument("--no-extras", action="store_true", help="skip baseline/single/cpu legs")
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--ncu", action="store_true", help="minimal run for a profiler launch list")
@@ -264,8 +267,16 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    # inputs are drawn before CUDA is touched (spawned worker pool)
-    items = S.batch_spec_parallel(nmat=args.nmat, seed=3 + 1000 * rank)
+    # inputs are drawn before CUDA is touched (spawned worker pool): one
+    # batch per rank, or (--split) this rank's share of one batch under the
+    # deterministic partition every rank computes alike
+    if args.split:
+        from paper_2609_40159_gb300 import shard
+        items = S.batch_spec_parallel(nmat=args.nmat, seed=3)
+        costs = [shard.system_cost(it.A.n, it.A.nnz, it.nrhs) for it in items]
+        items = [items[m] for m in shard.local_share(costs, rank, world)]
+    else:
+        items = S.batch_spec_parallel(nmat=args.nmat, seed=3 + 1000 * rank)
     if args.impl == "reference":
         if rank == 0:
             run_reference(args, items, rank)
@@ -377,7 +388,13 @@ def main():
         tm = torch.tensor([ms_step], device=dev)
         dist.all_reduce(tm, op=dist.ReduceOp.MAX)
         ms_step = float(tm.item())
-    value = world * step_bytes / (ms_step * 1e-3) / 1e9
+    # bytes of the whole job: every rank's own (reported outside the timed region)
+    job_bytes = world * step_bytes
+    if dist and args.split:
+        tb = torch.tensor([float(step_bytes)], device=dev, dtype=torch.float64)
+        dist.all_reduce(tb, op=dist.ReduceOp.SUM)
+        job_bytes = float(tb.item())
+    value = job_bytes / (ms_step * 1e-3) / 1e9
     status = P.handle().status()
 
     # correctness spot check of the timed buffers on two systems (device only)
@@ -449,7 +466,7 @@ def main():
         # the host results are the device path's (same kernels, same inputs)
         if not (torch.equal(hx[:1 << 20], x[:1 << 20].cpu()) and torch.equal(hgv[-(1 << 20):], gv[-(1 << 20):].cpu())):
             raise RuntimeError("end-to-end results differ from the device path")
-        e2e = {"value": world * step_bytes / (e2e_ms * 1e-3) / 1e9, "unit": "GB/s",
+        e2e = {"value": job_bytes / (e2e_ms * 1e-3) / 1e9, "unit": "GB/s",
                "ms_per_step": e2e_ms, "steps": Ke,
                "how": "sptrsv_batch_step_host per step (H2D of b and w from pinned host memory, fwd + "
                       "transpose solve, T^T, value gradient, D2H of x, g_b and g_vals; two device buffer "
@@ -472,7 +489,8 @@ def main():
         line = {
             "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": K,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "scaling": "strong" if args.split else "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
             "config": {"workload": WORKLOAD, "systems_per_gpu": len(items),
                        "rows_per_gpu": int(sum(A.n for A in mats)),
                        "nnz_per_gpu": int(sum(A.nnz for A in mats)),
@@ -480,9 +498,11 @@ def main():
                        "l2": "inputs 3.3 GB >> 129 MB L2; no flush needed",
                        "timing": "CUDA events on the launching stream around 3 CUDA-graph "
                                  "replays per step (fwd | transpose | T^T + gradient)",
-                       "parallelism": f"dp{world} (independent batches per GPU, no collective)"},
+                       "parallelism": (f"dp{world} (one batch split over the GPUs by greedy LPT, "
+                                       f"shard.partition; no collective in the data path)" if args.split else
+                                       f"dp{world} (independent batches per GPU, no collective)")},
             "gb_per_step": step_bytes / 1e9,
-            "solves_per_s": world * len(items) / (ms_step * 1e-3),
+            "solves_per_s": (args.nmat if args.split else world * len(items)) / (ms_step * 1e-3),
             "phase_ms": {"fwd": f_ms, "transpose": t_ms, "tt_and_grad": r_ms},
             "fwd_only_gbs": bf / (f_ms * 1e-3) / 1e9,
             "algorithmic_bytes": {"fwd_solve": bf, "transpose_solve": b_solveT, "step": step_bytes},
@@ -533,7 +553,8 @@ def _host_ms(fn, reps=3):
     return best
 
 
-def _single_config(P, A_h, dev, k, autotune, modes_run=("level_launch", "level", "syncfree"), modes=None):
+def _single_config(P, A_h, dev, k, autotune, modes_run=("level_launch", "level", "syncfree", "hybrid"),
+                   modes=None):
     """Analysis, rewrite (narrowest-level 1 %, chunks of 8 levels) and the
     forward solve in every mode (or the given ones) on the original and the
     rewritten DAG."""
@@ -558,7 +579,7 @@ def _single_config(P, A_h, dev, k, autotune, modes_run=("level_launch", "level",
         p = P.Plan(M, TT)
         nb = bytes_fwd(M.n, M.nnz, k, 8, M.n if TT is not None else 0, TT.nnz if TT is not None else 0)
         for mode in modes_run:
-            p.set(mode, 0, 0)
+            p.set(mode, 1 if mode == "hybrid" else 0, 0)
             ms = autotune.time_call(lambda: p.solve(b, out=x), reps=3, warmup=1)
             modes[f"{name}:{mode}"] = {"us": 1e3 * ms, "gbs": nb / (ms * 1e-3) / 1e9}
     res["fwd"] = modes
@@ -636,8 +657,8 @@ def _lap2d_config(P, dev, dt, autotune):
     for name, (M, TT) in {"orig": (A, None), "rewritten": (Lp, T)}.items():
         p = P.Plan(M, TT)
         nb = bytes_fwd(M.n, M.nnz, 1, wv, M.n if TT is not None else 0, TT.nnz if TT is not None else 0)
-        for mode in ("level_launch", "level", "syncfree", "block"):
-            p.set(mode, 32, 1)
+        for mode in ("level_launch", "level", "syncfree", "block", "hybrid"):
+            p.set(mode, 4 if mode == "hybrid" else 32, 1)
             ms = autotune.time_call(lambda: p.solve(b, out=x), reps=5, warmup=2)
             msc = _time_cold(lambda: p.solve(b, out=x), 3, flush)
             modes[f"{name}:{mode}"] = {"us": 1e3 * ms, "us_cold_l2": 1e3 * msc, "gbs": nb / (ms * 1e-3) / 1e9,
@@ -733,7 +754,7 @@ def run_extras(P, items, mats, dev, bf_total):
     out["powerlaw_4M_f64"] = _single_config(P, S.powerlaw(4_000_000, alpha=2.1, seed=2), dev, 1, autotune)
     # the nnz-matched variant of the power-law DAG (mean ~9 off-diagonals per row)
     out["powerlaw_4M_alpha1.7_f64"] = _single_config(P, S.powerlaw(4_000_000, alpha=1.7, seed=2), dev, 1, autotune,
-                                                     modes=("level", "syncfree"))
+                                                     modes=("level", "syncfree", "hybrid"))
     out["lap3d_128_f64_diff_k8"] = _diff_config(P, S.lap3d(128), dev, 8, autotune)
     # --- CPU oracle on the host cores (whole batch, fwd + adjoint, one pass)
     t0 = time.perf_counter()

@@ -90,7 +90,14 @@ typedef enum {
     /* Synchronisation-free solve inside one thread block: flags and recent
      * solution values live in shared memory; for deep, narrow systems where
      * the cross-SM flag round trip would dominate.                           */
-    SPTRSV_MODE_BLOCK = 4
+    SPTRSV_MODE_BLOCK = 4,
+    /* Hybrid of the level-set and synchronisation-free schedules (Section 7,
+     * related work): rows in level order as in LEVEL_PERSISTENT; a thick
+     * level waits for every earlier level, a maximal run of consecutive thin
+     * levels (fewer rows than the plan's thin_rows) waits once for the rows
+     * before the run, and inside the run each row waits only for its own
+     * predecessors' ready flags.                                             */
+    SPTRSV_MODE_HYBRID = 5
 } sptrsv_mode;
 
 typedef struct {
@@ -258,6 +265,14 @@ sptrsv_status sptrsv_batch_plan_create(sptrsv_handle handle, int32_t nmat, const
                                        const sptrsv_csr *Ts, const int32_t *nrhs,
                                        const sptrsv_plan_opts *opts, sptrsv_plan *plan);
 sptrsv_status sptrsv_batch_offsets(sptrsv_plan plan, int64_t *rhs_offset, int64_t *vals_offset);
+/* Thin-level threshold of SPTRSV_MODE_HYBRID: levels with fewer rows than
+ * thin_rows form the synchronisation-free runs (1 = no thin level, i.e. the
+ * level-persistent schedule; 0 = automatic = every level thin, one run:
+ * barriers before thick levels were slower on every workload measured).
+ * Returns SPTRSV_EINVAL for a negative value or a batched plan.
+ * Synchronises.                                                           */
+sptrsv_status sptrsv_plan_set_thin_rows(sptrsv_plan plan, int32_t thin_rows);
+
 /* Re-tunes a batched plan (used by the autotuner; no analysis is repeated).
  *   rows_per_warp  host, nmat entries (1,2,4,8,16,32; 0 = keep) or NULL:
  *                  row-group width of every system;

@@ -32,6 +32,7 @@ SPTRSV_MODE_LEVEL_LAUNCH = 1
 SPTRSV_MODE_LEVEL_PERSISTENT = 2
 SPTRSV_MODE_SYNCFREE = 3
 SPTRSV_MODE_BLOCK = 4
+SPTRSV_MODE_HYBRID = 5
 
 MODE_NAMES = {
     "auto": SPTRSV_MODE_AUTO,
@@ -40,6 +41,7 @@ MODE_NAMES = {
     "level_persistent": SPTRSV_MODE_LEVEL_PERSISTENT,
     "syncfree": SPTRSV_MODE_SYNCFREE,
     "block": SPTRSV_MODE_BLOCK,
+    "hybrid": SPTRSV_MODE_HYBRID,
 }
 
 
@@ -97,6 +99,7 @@ _SIGS = {
     "sptrsv_plan_destroy": [sptrsv_plan],
     "sptrsv_plan_info": [sptrsv_plan, _PI32, _PI32, _PI32, _PI32],
     "sptrsv_plan_set": [sptrsv_plan, _I32, _I32, _I32],
+    "sptrsv_plan_set_thin_rows": [sptrsv_plan, _I32],
     "sptrsv_solve": [sptrsv_plan, _P, _P, _I32, _I64],
     "sptrsv_solve_transpose": [sptrsv_plan, _P, _P, _I32, _I64],
     "sptrsv_grad_vals": [sptrsv_plan, _P, _P, _I32, _I64, _P],

@@ -256,6 +256,10 @@ class Plan:
         mode = L.MODE_NAMES[mode] if isinstance(mode, str) else int(mode)
         L.check(L.lib().sptrsv_plan_set(self.p, mode, rows_per_warp, rhs_tile), "sptrsv_plan_set")
 
+    def set_thin_rows(self, thin_rows: int = 0):
+        """Thin-level threshold of the hybrid mode (0 = automatic)."""
+        L.check(L.lib().sptrsv_plan_set_thin_rows(self.p, int(thin_rows)), "sptrsv_plan_set_thin_rows")
+
     def withhold(self, row: int):
         L.check(L.lib().sptrsv_debug_withhold_row(self.p, row))
 

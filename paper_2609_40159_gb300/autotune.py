@@ -20,7 +20,7 @@ import torch
 from . import _lib as L
 from .api import BatchPlan, Plan
 
-CANDIDATE_MODES = ("level", "syncfree", "block")
+CANDIDATE_MODES = ("level", "syncfree", "block", "hybrid")
 CANDIDATE_RPW = (1, 4, 8, 16, 32)
 
 

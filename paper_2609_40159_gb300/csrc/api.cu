@@ -127,6 +127,10 @@ struct sptrsv_plan_st {
     uint32_t *d_flags = nullptr;
     int grid_level = 0, grid_sf = 0;
     int32_t max_width = 0;
+    // hybrid schedule: thin-level threshold (0 = automatic) and, per
+    // direction, the first level of the thin run holding every level
+    int32_t thin_rows = 0, seg_rows = -1;
+    int32_t *d_seg[2] = {nullptr, nullptr};
     // batched
     std::vector<PlanMat> mats;
     std::vector<int64_t> rhs_off, vals_off, row_off;
@@ -431,17 +435,52 @@ sptrsv_status ensure_chunks(sptrsv_plan p)
     return SPTRSV_OK;
 }
 
+// Thin-run heads of the hybrid schedule, per direction (processing order:
+// forward = level order, transpose = reverse level order): seg[l] = l for a
+// thick level, the run's first level for a level of a run of consecutive
+// thin levels.
+sptrsv_status ensure_hybrid(sptrsv_plan p)
+{
+    const PlanMat &M = p->M;
+    const int32_t L = M.nlevels;
+    // automatic: every level thin (one synchronisation-free run in level
+    // order); barriers before thick levels measured slower on every
+    // workload tried (2D/3D Laplacians, power-law DAG, banded)
+    const int32_t thr = p->thin_rows > 0 ? p->thin_rows : INT32_MAX;
+    if (p->seg_rows == thr && p->d_seg[0]) return SPTRSV_OK;
+    cudaError_t e = cudaSuccess;
+    for (int d = 0; d < 2 && e == cudaSuccess; ++d)
+        if (!p->d_seg[d]) e = p->alloc(&p->d_seg[d], sizeof(int32_t) * (size_t)std::max(L, 1));
+    if (e != cudaSuccess) return from_cuda(e);
+    std::vector<int32_t> seg((size_t)std::max(L, 1));
+    for (int d = 0; d < 2 && e == cudaSuccess; ++d) {
+        for (int32_t k = 0; k < L; ++k) {
+            const int32_t l = d == 0 ? k : L - 1 - k;  // level of processing index k
+            const bool thin = M.h_level_ptr[l + 1] - M.h_level_ptr[l] < thr;
+            const int32_t l_prev = d == 0 ? k - 1 : L - k;
+            const bool prev_thin = k > 0 && M.h_level_ptr[l_prev + 1] - M.h_level_ptr[l_prev] < thr;
+            seg[k] = thin && prev_thin ? seg[k - 1] : k;
+        }
+        if (L > 0) e = cudaMemcpy(p->d_seg[d], seg.data(), sizeof(int32_t) * L, cudaMemcpyHostToDevice);
+    }
+    if (e != cudaSuccess) return from_cuda(e);
+    p->seg_rows = thr;
+    return SPTRSV_OK;
+}
+
 // Mode from the mean level width: narrow (deep) systems stay on one SM,
 // very wide levels go level by level (row-order sync-free solving keeps
 // only the rows in flight near the wavefront and idles on wide, far-reaching
-// levels: 9x slower than level order on the 3D Laplacian), the rest sync-free.
+// levels: 9x slower than level order on the 3D Laplacian), the rest takes
+// the hybrid schedule (synchronisation-free in level order: 2x faster than
+// row order on the power-law DAG, 17 % on the 2D Laplacian).
 int auto_mode(const PlanMat &M)
 {
     if (M.L.n == 0 || M.nlevels == 0) return SPTRSV_MODE_SYNCFREE;
     const double width = (double)M.L.n / M.nlevels;
     if (width < 48.0) return SPTRSV_MODE_BLOCK;
     if (width >= 2048.0) return SPTRSV_MODE_LEVEL_PERSISTENT;
-    return SPTRSV_MODE_SYNCFREE;
+    return SPTRSV_MODE_HYBRID;
 }
 
 template <class T>
@@ -475,6 +514,15 @@ sptrsv_status solve_impl(sptrsv_plan p, const void *b, void *x, int32_t nrhs, in
         const int64_t want = (2 * (int64_t)p->max_width / p->rpw + 7) / 8;  // blocks of 8 warps
         const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(p->grid_level, want));
         e = solve_level_persistent<T>(A, S, R, p->rpw, kt, trans, sy, grid, s);
+        break;
+    }
+    case SPTRSV_MODE_HYBRID: {
+        sptrsv_status st = ensure_chunks(p);
+        if (st == SPTRSV_OK) st = ensure_hybrid(p);
+        if (st != SPTRSV_OK) return st;
+        Sched S{M.d_perm, M.d_level_ptr, M.nlevels, trans ? p->d_chunk_tr : p->d_chunk_fwd,
+                ((int64_t)M.L.n + p->rpw - 1) / p->rpw, p->d_seg[trans ? 1 : 0], M.d_lev};
+        e = solve_level_persistent<T>(A, S, R, p->rpw, kt, trans, sy, p->grid_level, s);
         break;
     }
     case SPTRSV_MODE_BLOCK: {
@@ -627,8 +675,11 @@ extern "C" sptrsv_status sptrsv_plan_create(sptrsv_handle h, const sptrsv_csr *L
         if (e != cudaSuccess) { sptrsv_plan_destroy(p); return from_cuda(e); }
         p->rpw = default_rpw(L->n, L->nnz, (int64_t)nlong);
     }
+    // the hybrid schedule waits row by row on flags: one row per warp, so
+    // that a warp is not held up by the slowest of several rows
+    if (p->mode == SPTRSV_MODE_HYBRID && !valid_rpw(o.rows_per_warp)) p->rpw = 1;
     p->kt = valid_kt(o.rhs_tile) ? o.rhs_tile : 16;
-    if (p->mode < SPTRSV_MODE_LEVEL_LAUNCH || p->mode > SPTRSV_MODE_BLOCK) { sptrsv_plan_destroy(p); return SPTRSV_EINVAL; }
+    if (p->mode < SPTRSV_MODE_LEVEL_LAUNCH || p->mode > SPTRSV_MODE_HYBRID) { sptrsv_plan_destroy(p); return SPTRSV_EINVAL; }
     p->grid_level = persistent_grid_level(1, p->dtype == SPTRSV_F64, h->di);
     {
         // warps beyond about twice the widest level only poll the progress
@@ -663,6 +714,13 @@ extern "C" sptrsv_status sptrsv_plan_destroy(sptrsv_plan p)
     return SPTRSV_OK;
 }
 
+extern "C" sptrsv_status sptrsv_plan_set_thin_rows(sptrsv_plan p, int32_t thin_rows)
+{
+    if (!p || p->batched || thin_rows < 0) return SPTRSV_EINVAL;
+    p->thin_rows = thin_rows;
+    return p->mode == SPTRSV_MODE_HYBRID ? ensure_hybrid(p) : SPTRSV_OK;
+}
+
 extern "C" sptrsv_status sptrsv_plan_info(sptrsv_plan p, int32_t *nlevels, int32_t *mode,
                                           int32_t *rows_per_warp, int32_t *rhs_tile)
 {
@@ -685,7 +743,7 @@ extern "C" sptrsv_status sptrsv_plan_info(sptrsv_plan p, int32_t *nlevels, int32
 extern "C" sptrsv_status sptrsv_plan_set(sptrsv_plan p, int32_t mode, int32_t rows_per_warp, int32_t rhs_tile)
 {
     if (!p || p->batched) return SPTRSV_EINVAL;
-    if (mode < SPTRSV_MODE_AUTO || mode > SPTRSV_MODE_BLOCK) return SPTRSV_EINVAL;
+    if (mode < SPTRSV_MODE_AUTO || mode > SPTRSV_MODE_HYBRID) return SPTRSV_EINVAL;
     if (rows_per_warp != 0 && !valid_rpw(rows_per_warp)) return SPTRSV_EINVAL;
     if (rhs_tile != 0 && !valid_kt(rhs_tile)) return SPTRSV_EINVAL;
     p->mode = mode == SPTRSV_MODE_AUTO ? auto_mode(p->M) : mode;

@@ -105,7 +105,45 @@ __device__ __forceinline__ void gather_row(const Sys<T> &A, const Rhs<T> &R, int
     }
 }
 
+// The same for a row of a thin run whose earlier levels may still be in
+// progress: a dependency in the run (processing level >= h) is read once
+// its ready flag is set.  Returns false when a wait gave up.
+template <class T, int KT, bool TR>
+__device__ __forceinline__ bool gather_row_run(const Sys<T> &A, const Rhs<T> &R, const Sched &S, int h, int i,
+                                               int a, int e, int sl, int lpr, int r0, int kt, T (&acc)[KT],
+                                               const SyncArgs &sy, uint32_t epoch)
+{
+    if (!TR && has_trow(A, i)) {
+        const int tb = A.trp[i], te = A.trp[i + 1];
+        for (int p = tb + sl; p < te; p += lpr) {
+            const T tv = ldro(A.tv + p);
+            const T *bb = R.b + (int64_t)ldro(A.tci + p) * R.ld + r0;
+#pragma unroll
+            for (int r = 0; r < KT; ++r)
+                if (r < kt) acc[r] -= tv * bb[r];
+        }
+    }
+    for (int p = a + sl; p < e; p += lpr) {
+        const int j = RV<T, TR>::col(A, p);
+        const int lj = ldro(S.lev + j);
+        if ((TR ? S.nlevels - 1 - lj : lj) >= h && !wait_flag(sy.flags + j, epoch, sy.w)) return false;
+        const T vv = RV<T, TR>::val(A, p);
+        const T *xx = R.x + (int64_t)j * R.ld + r0;
+#pragma unroll
+        for (int r = 0; r < KT; ++r)
+            if (r < kt) acc[r] += vv * xx[r];
+    }
+    return true;
+}
+
 // ------------------------------------------------ persistent level set
+// Row groups in level order (transpose: reverse level order) from a
+// ticket; a group of level l waits until the grid-wide count of completed
+// rows covers every earlier level.  Hybrid schedule (S.seg set): a level
+// inside a run of thin levels waits only for the rows before the run, and
+// its dependencies inside the run are waited for one by one through the
+// rows' ready flags (the synchronisation-free protocol), so that the thin
+// levels of a run overlap instead of taking one grid-wide hop each.
 template <class T, int KT, bool TR>
 __global__ void __launch_bounds__(256)
 k_level_persistent(Sys<T> A, Sched S, Rhs<T> R, int rpw, SyncArgs sy)
@@ -114,6 +152,7 @@ k_level_persistent(Sys<T> A, Sched S, Rhs<T> R, int rpw, SyncArgs sy)
     const int lpr = 32 / rpw;
     const int g = lane / lpr, sl = lane & (lpr - 1);
     const int n = A.n, L = S.nlevels;
+    const uint32_t epoch = (uint32_t)sy.ctl->epoch;
     for (;;) {
         unsigned long long c = 0;
         if (lane == 0) c = atomicAdd(&sy.ctl->ticket, 1ull);
@@ -134,8 +173,12 @@ k_level_persistent(Sys<T> A, Sched S, Rhs<T> R, int rpw, SyncArgs sy)
             const int a = active ? RV<T, TR>::beg(A, i) : 0;
             const int e = active ? RV<T, TR>::end(A, i) : 0;
             const T rinv = active ? T(1) / RV<T, TR>::diag(A, a, e) : T(0);
+            // hybrid: the run's first level h, whose start is all this
+            // group waits for (h == l: a thick level or a run's first level)
+            const int h = S.seg ? S.seg[l] : l;
+            const int wstart = h == l ? lstart : (TR ? n - S.level_ptr[L - h] : S.level_ptr[h]);
             int ok = 1;
-            if (lane == 0) ok = wait_count(&sy.ctl->progress, (unsigned long long)lstart, sy.w);
+            if (lane == 0) ok = wait_count(&sy.ctl->progress, (unsigned long long)wstart, sy.w);
             ok = __shfl_sync(SPT_FULL_MASK, ok, 0);
             if (!ok) return;
             __syncwarp();
@@ -144,7 +187,14 @@ k_level_persistent(Sys<T> A, Sched S, Rhs<T> R, int rpw, SyncArgs sy)
                 T acc[KT];
 #pragma unroll
                 for (int r = 0; r < KT; ++r) acc[r] = T(0);
-                if (active) gather_row<T, KT, TR>(A, R, i, a, e, sl, lpr, r0, kt, acc);
+                bool got = true;
+                if (active) {
+                    if (h < l)
+                        got = gather_row_run<T, KT, TR>(A, R, S, h, i, a, e, sl, lpr, r0, kt, acc, sy, epoch);
+                    else
+                        gather_row<T, KT, TR>(A, R, i, a, e, sl, lpr, r0, kt, acc);
+                }
+                if (__any_sync(SPT_FULL_MASK, !got)) return;
                 group_reduce<T, KT>(acc, lpr);
                 if (active && sl == 0) {
                     const T *bb = R.b + (int64_t)i * R.ld + r0;
@@ -152,6 +202,8 @@ k_level_persistent(Sys<T> A, Sched S, Rhs<T> R, int rpw, SyncArgs sy)
 #pragma unroll
                     for (int r = 0; r < KT; ++r)
                         if (r < kt) xx[r] = (bb[r] - acc[r]) * rinv;
+                    // hybrid: the row's ready flag (after its last tile)
+                    if (S.seg && r0 + KT >= R.k && i != sy.withhold) st_release(sy.flags + i, epoch);
                 }
             }
             // test hook: a withheld row is never counted, so that every

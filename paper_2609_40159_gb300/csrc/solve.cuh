@@ -34,6 +34,11 @@ struct Sched {
     int32_t nlevels;
     const int32_t *chunk_level;  // level of the first row of every row group
     int64_t nchunks;
+    // hybrid schedule (null: every level waits for all earlier levels):
+    // seg[l] = first level (in processing order) of the run of thin levels
+    // that holds level l (l itself for a thick level); lev = row levels
+    const int32_t *seg;
+    const int32_t *lev;
 };
 
 template <class T> struct Rhs {

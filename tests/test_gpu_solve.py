@@ -14,7 +14,7 @@ from helpers import TOL, cases_small, relerr, widened
 
 pytestmark = pytest.mark.gpu
 
-MODES = ["level_launch", "level", "syncfree", "block"]
+MODES = ["level_launch", "level", "syncfree", "block", "hybrid"]
 RPWS = [1, 4, 32]
 KS = [1, 3, 32]
 
@@ -221,7 +221,7 @@ def test_full_size_powerlaw():
         assert relerr(plan.solve(b).cpu().numpy(), x_ref) <= 1e-12, mode
 
 
-@pytest.mark.parametrize("mode", ["level", "syncfree", "block"])
+@pytest.mark.parametrize("mode", ["level", "syncfree", "block", "hybrid"])
 def test_bounded_wait_reports_timeout(mode):
     """A row that is never published (test hook; the level-persistent mode
     leaves it out of its progress counter): the solve gives up after the
@@ -243,13 +243,39 @@ def test_bounded_wait_reports_timeout(mode):
     assert relerr(x.cpu().numpy(), oracle.solve(A_h, b.cpu().numpy())) <= 1e-12
 
 
+@pytest.mark.parametrize("name", ["lap2d_97", "lap3d_23", "powerlaw", "wide_level", "chain", "band_wide"])
+def test_hybrid_thin_thresholds(name):
+    """The hybrid schedule at every extreme of its thin-level threshold --
+    no thin level (the level-persistent schedule), a few rows, a level of
+    the widest size, every level thin (one synchronisation-free run) -- and
+    with 1, 3 and 16 right-hand sides, forward and transpose, vs the
+    oracle."""
+    import paper_2609_40159_gb300 as P
+    A_h = _case(name)
+    A = P.Matrix.from_host(A_h)
+    plan = P.Plan(A, mode="hybrid", transpose=True)
+    an = oracle.analyze(A_h)
+    widest = int(np.diff(an["level_ptr"]).max())
+    for k in (1, 3, 16):
+        b_h = S.rhs(A_h.n, k, seed=k)
+        b = torch.as_tensor(b_h).cuda()
+        x_ref, g_ref = oracle.solve(A_h, b_h), oracle.solve_transpose(A_h, b_h)
+        for thin in (1, 8, 64, widest, 2**31 - 1, 0):
+            plan.set_thin_rows(thin)
+            for rpw in (1, 32):
+                plan.set("hybrid", rpw, 4)
+                assert relerr(plan.solve(b).cpu().numpy(), x_ref) <= 1e-12, (thin, rpw, k)
+                assert relerr(plan.solve_transpose(b).cpu().numpy(), g_ref) <= 1e-12, ("T", thin, rpw, k)
+    assert P.handle().status() == 0
+
+
 def test_cuda_graph_replay():
     import paper_2609_40159_gb300 as P
     A_h = S.band_random(50_000, 64, 4, 16, seed=11)
     A = P.Matrix.from_host(A_h)
     b = torch.as_tensor(S.rhs(A_h.n, 2, seed=3)).cuda()
     x = torch.empty_like(b)
-    for mode in ["level", "syncfree", "block"]:
+    for mode in ["level", "syncfree", "block", "hybrid"]:
         plan = P.Plan(A, mode=mode)
         plan.solve(b, out=x)  # warm-up outside capture
         torch.cuda.synchronize()
@@ -268,7 +294,7 @@ def test_cuda_graph_replay():
             assert relerr(x.cpu().numpy(), oracle.solve(A_h, b.cpu().numpy())) <= 1e-12, mode
 
 
-@pytest.mark.parametrize("mode", ["auto", "level", "syncfree", "block"])
+@pytest.mark.parametrize("mode", ["auto", "level", "syncfree", "block", "hybrid"])
 @pytest.mark.parametrize("k", [1, 4])
 def test_upper_triangular_solve(mode, k):
     """U x = b for an upper-triangular U (rows store the diagonal first),
