@@ -53,7 +53,9 @@ typedef enum {
     SPTRSV_ENOMEM = 6,     /* device allocation failed                       */
     SPTRSV_ETIMEOUT = 7,   /* a bounded device wait gave up                  */
     SPTRSV_ECUDA = 8,      /* a CUDA runtime call failed                     */
-    SPTRSV_ENOTSUP = 9     /* option not supported for this input            */
+    SPTRSV_ENOTSUP = 9,    /* option not supported for this input            */
+    SPTRSV_ERANGE = 10     /* an index out of its array's range, found by the
+                              bounds checks of an SPTRSV_CHECKED build       */
 } sptrsv_status;
 
 typedef enum { SPTRSV_F64 = 0, SPTRSV_F32 = 1 } sptrsv_dtype;
@@ -244,6 +246,23 @@ sptrsv_status sptrsv_solve(sptrsv_plan plan, const void *b, void *x, int32_t nrh
 sptrsv_status sptrsv_solve_transpose(sptrsv_plan plan, const void *gx, void *gb, int32_t nrhs,
                                      int64_t ld);
 
+/* Multi-right-hand-side solve (SpTRSM) in either dense layout:
+ *   SPTRSV_ROW_MAJOR  [n x nrhs], element (i, r) at i * ld + r, ld >= nrhs
+ *                     (the layout of sptrsv_solve);
+ *   SPTRSV_COL_MAJOR  every right-hand side a contiguous column: element
+ *                     (i, r) at r * ld + i, ld >= n.
+ * transpose = 0: x = L^{-1} b (or L^{-1} (b + T b)); 1: x = L^{-T} b as
+ * sptrsv_solve_transpose (needs build_transpose).  A column-major block is
+ * converted to the row-major layout the kernels gather from (each row's
+ * right-hand sides contiguous) by tiled shared-memory transposes into a
+ * plan-owned buffer of 2 n nrhs elements, allocated on first use and when
+ * nrhs grows (so that call synchronises), and the solution is converted
+ * back.  Returns SPTRSV_EINVAL for another layout or ld too small.
+ * Asynchronous otherwise.                                                  */
+typedef enum { SPTRSV_ROW_MAJOR = 0, SPTRSV_COL_MAJOR = 1 } sptrsv_layout;
+sptrsv_status sptrsv_solve_layout(sptrsv_plan plan, const void *b, void *x, int32_t nrhs, int64_t ld,
+                                  int32_t layout, int32_t transpose);
+
 /* Value gradient on L's pattern: gvals[p] = -sum_r gb[i,r] * x[j,r] for the
  * stored entry p = (i, j), diagonal included.  Asynchronous.                */
 sptrsv_status sptrsv_grad_vals(sptrsv_plan plan, const void *gb, const void *x, int32_t nrhs,
@@ -345,6 +364,21 @@ sptrsv_status sptrsv_batch_step_host(sptrsv_plan plan, const void *b, const void
 /* Waits for every step enqueued by sptrsv_batch_step_host and returns the
  * handle's device status (SPTRSV_OK, or e.g. SPTRSV_ETIMEOUT).             */
 sptrsv_status sptrsv_batch_step_wait(sptrsv_plan plan);
+
+/* ------------------------------------------------------------ bounds checks */
+/* The library also builds as a bounds-checked debug variant
+ * (libsptrsv_gb300_checked.so, compiled with SPTRSV_CHECKED): every index a
+ * solve gathers through -- row extents, column indices, positions of the
+ * level order, levels, columns of T -- is checked against its array's
+ * range; an index outside is recorded as SPTRSV_ERANGE in the handle's
+ * status word and replaced by a valid one, so that the access stays inside
+ * the array.  sptrsv_checked_build returns 1 in that variant, 0 in the
+ * product library (where the checks compile to nothing).
+ * sptrsv_debug_check_index runs one checked index through the same check
+ * (index against [0, n), 1 <= n <= 32), for tests of the reporting path:
+ * in the checked variant an index outside records SPTRSV_ERANGE.          */
+int32_t sptrsv_checked_build(void);
+sptrsv_status sptrsv_debug_check_index(sptrsv_handle handle, int32_t index, int32_t n);
 
 /* --------------------------------------------------- allocation-free solve */
 /* The paper has no counterpart of this entry point; it exists for callers

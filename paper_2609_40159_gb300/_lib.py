@@ -6,11 +6,14 @@ has not been built (there is no CPU fallback).
 """
 from __future__ import annotations
 
+import atexit
 import ctypes as C
 import os
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libsptrsv_gb300.so")
+# bounds-checked debug variant (built alongside; see sptrsv_checked_build)
+LIB_CHECKED_PATH = os.path.join(_HERE, "libsptrsv_gb300_checked.so")
 
 # status codes
 SPTRSV_OK = 0
@@ -23,6 +26,7 @@ SPTRSV_ENOMEM = 6
 SPTRSV_ETIMEOUT = 7
 SPTRSV_ECUDA = 8
 SPTRSV_ENOTSUP = 9
+SPTRSV_ERANGE = 10
 
 SPTRSV_F64 = 0
 SPTRSV_F32 = 1
@@ -102,6 +106,7 @@ _SIGS = {
     "sptrsv_plan_set_thin_rows": [sptrsv_plan, _I32],
     "sptrsv_solve": [sptrsv_plan, _P, _P, _I32, _I64],
     "sptrsv_solve_transpose": [sptrsv_plan, _P, _P, _I32, _I64],
+    "sptrsv_solve_layout": [sptrsv_plan, _P, _P, _I32, _I64, _I32, _I32],
     "sptrsv_grad_vals": [sptrsv_plan, _P, _P, _I32, _I64, _P],
     "sptrsv_tt_apply": [sptrsv_plan, _P, _P, _I32, _I64],
     "sptrsv_batch_plan_create": [sptrsv_handle, _I32, C.POINTER(sptrsv_csr), C.POINTER(sptrsv_csr),
@@ -120,12 +125,15 @@ _SIGS = {
     "sptrsv_debug_withhold_level": [sptrsv_handle, _I32, _I64],
     "sptrsv_batch_trace": [sptrsv_plan, _PI64],
     "sptrsv_solve_noalloc": [C.POINTER(sptrsv_csr), _P, _P, _I32, _I64, _P],
+    "sptrsv_debug_check_index": [sptrsv_handle, _I32, _I32],
 }
 SPTRSV_NOALLOC_MAX_ROWS = 1 << 20
 SPTRSV_BATCH_INORDER = 1
+SPTRSV_ROW_MAJOR = 0
+SPTRSV_COL_MAJOR = 1
 SPTRSV_BATCH_LEVEL = 2
 
-DECLARED = sorted(list(_SIGS) + ["sptrsv_status_string"])
+DECLARED = sorted(list(_SIGS) + ["sptrsv_status_string", "sptrsv_checked_build"])
 
 
 def load(path: str = LIB_PATH):
@@ -142,10 +150,28 @@ def load(path: str = LIB_PATH):
         f.restype = C.c_int
     lib.sptrsv_status_string.argtypes = [C.c_int]
     lib.sptrsv_status_string.restype = C.c_char_p
+    lib.sptrsv_checked_build.argtypes = []
+    lib.sptrsv_checked_build.restype = C.c_int32
     return lib
 
 
 _lib = None
+_exiting = False
+
+
+def _mark_exit():
+    global _exiting
+    _exiting = True
+
+
+# Objects still alive when the interpreter exits (e.g. held by a traceback)
+# must not call into the library from their finalisers: the CUDA runtime may
+# already be torn down, and the process returns the device memory anyway.
+atexit.register(_mark_exit)
+
+
+def exiting() -> bool:
+    return _exiting
 
 
 def lib():

@@ -84,7 +84,7 @@ class Handle:
 
     def __del__(self):
         try:
-            if getattr(self, "h", None):
+            if getattr(self, "h", None) and not L.exiting():
                 L.lib().sptrsv_destroy(self.h)
         except Exception:
             pass
@@ -256,6 +256,22 @@ class Plan:
         mode = L.MODE_NAMES[mode] if isinstance(mode, str) else int(mode)
         L.check(L.lib().sptrsv_plan_set(self.p, mode, rows_per_warp, rhs_tile), "sptrsv_plan_set")
 
+    def solve_columns(self, B, transpose=False, out=None):
+        """Multi-right-hand-side solve in the column-major layout: B is a
+        [k, n] CUDA tensor whose row r is right-hand side r (rows may be
+        padded: stride(0) >= n); returns X of the same layout with
+        X[r] = L^{-1} B[r] (transpose: L^{-T} B[r]).  See
+        sptrsv_solve_layout."""
+        n = self.A.n
+        if B.dim() != 2 or B.shape[1] != n or B.stride(1) != 1 or B.dtype != self.A.dtype or not B.is_cuda:
+            raise ValueError("B must be a [k, n] CUDA tensor of the matrix dtype with unit stride along n")
+        X = out if out is not None else torch.empty_strided(B.shape, B.stride(), dtype=B.dtype, device=B.device)
+        if X.shape != B.shape or X.stride() != B.stride():
+            raise ValueError("out must have B's shape and strides")
+        L.check(L.lib().sptrsv_solve_layout(self.p, _ptr(B), _ptr(X), B.shape[0], B.stride(0),
+                                            L.SPTRSV_COL_MAJOR, 1 if transpose else 0), "sptrsv_solve_layout")
+        return X
+
     def set_thin_rows(self, thin_rows: int = 0):
         """Thin-level threshold of the hybrid mode (0 = automatic)."""
         L.check(L.lib().sptrsv_plan_set_thin_rows(self.p, int(thin_rows)), "sptrsv_plan_set_thin_rows")
@@ -307,7 +323,7 @@ class Plan:
 
     def __del__(self):
         try:
-            if getattr(self, "p", None):
+            if getattr(self, "p", None) and not L.exiting():
                 L.lib().sptrsv_plan_destroy(self.p)
         except Exception:
             pass
@@ -474,7 +490,7 @@ class BatchPlan:
 
     def __del__(self):
         try:
-            if getattr(self, "p", None):
+            if getattr(self, "p", None) and not L.exiting():
                 L.lib().sptrsv_plan_destroy(self.p)
         except Exception:
             pass

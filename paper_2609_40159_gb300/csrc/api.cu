@@ -131,6 +131,10 @@ struct sptrsv_plan_st {
     // direction, the first level of the thin run holding every level
     int32_t thin_rows = 0, seg_rows = -1;
     int32_t *d_seg[2] = {nullptr, nullptr};
+    // row-major copies of a column-major right-hand-side block and its
+    // solution (sptrsv_solve_layout), grown on demand
+    void *d_lay = nullptr;
+    size_t lay_bytes = 0;
     // batched
     std::vector<PlanMat> mats;
     std::vector<int64_t> rhs_off, vals_off, row_off;
@@ -248,6 +252,7 @@ extern "C" const char *sptrsv_status_string(sptrsv_status s)
     case SPTRSV_ETIMEOUT: return "a bounded device wait gave up";
     case SPTRSV_ECUDA: return "CUDA error";
     case SPTRSV_ENOTSUP: return "not supported";
+    case SPTRSV_ERANGE: return "index out of range (bounds-checked build)";
     }
     return "unknown status";
 }
@@ -341,9 +346,11 @@ sptrsv_status analyze_into(sptrsv_handle h, const sptrsv_csr &L, int32_t *lev, i
     return from_cuda(e);
 }
 
-template <class T> Sys<T> sys_of(const PlanMat &M)
+template <class T> Sys<T> sys_of(const PlanMat &M, int *chk)
 {
     Sys<T> A;
+    A.nnz = M.L.nnz;
+    A.chk = chk;
     A.n = M.L.n;
     A.rp = M.L.row_ptr; A.ci = M.L.col_idx; A.v = (const T *)M.L.vals;
     A.cp = M.d_cp; A.crow = M.d_crow; A.tmap = M.d_tmap; A.cv = (const T *)M.d_cv;
@@ -491,7 +498,7 @@ sptrsv_status solve_impl(sptrsv_plan p, const void *b, void *x, int32_t nrhs, in
     if (!b || !x || nrhs < 1 || ld < nrhs) return SPTRSV_EINVAL;
     if (trans && !p->have_csc) return SPTRSV_ENOTSUP;
     cudaStream_t s = p->h->stream;
-    Sys<T> A = sys_of<T>(M);
+    Sys<T> A = sys_of<T>(M, p->h->d_status);
     Rhs<T> R{(const T *)b, (T *)x, ld, nrhs};
     if (trans) {
         cudaError_t eg = csc_values<T>(M.d_tmap, (const T *)M.L.vals, (T *)M.d_cv, M.L.nnz, s);
@@ -709,6 +716,7 @@ extern "C" sptrsv_status sptrsv_plan_destroy(sptrsv_plan p)
             cudaStreamSynchronize(st);
             cudaStreamDestroy(st);
         }
+    if (p->d_lay) cudaFree(p->d_lay);
     for (void *q : p->owned) cudaFree(q);
     delete p;
     return SPTRSV_OK;
@@ -770,6 +778,53 @@ extern "C" sptrsv_status sptrsv_solve_transpose(sptrsv_plan p, const void *gx, v
                                   : solve_impl<float>(p, gx, gb, nrhs, ld, true);
 }
 
+namespace {
+template <class T>
+sptrsv_status solve_colmajor(sptrsv_plan p, const void *b, void *x, int32_t nrhs, int64_t ld, bool trans)
+{
+    const int64_t n = p->M.L.n;
+    const size_t need = 2 * sizeof(T) * (size_t)n * (size_t)nrhs;
+    cudaStream_t s = p->h->stream;
+    if (need > p->lay_bytes) {
+        cudaError_t e = cudaStreamSynchronize(s);  // the old buffer may still be in use
+        if (e == cudaSuccess && p->d_lay) e = cudaFree(p->d_lay);
+        p->d_lay = nullptr;
+        p->lay_bytes = 0;
+        if (e == cudaSuccess) e = cudaMalloc(&p->d_lay, need);
+        if (e != cudaSuccess) return from_cuda(e);
+        p->lay_bytes = need;
+    }
+    T *rb = static_cast<T *>(p->d_lay);
+    T *rx = rb + (size_t)n * nrhs;
+    // column r of b (element (i, r) at r * ld + i) -> row-major [n x nrhs]
+    cudaError_t e = transpose_dense<T>(static_cast<const T *>(b), ld, rb, nrhs, nrhs, n, s);
+    if (e != cudaSuccess) return from_cuda(e);
+    sptrsv_status st = solve_impl<T>(p, rb, rx, nrhs, nrhs, trans);
+    if (st != SPTRSV_OK) return st;
+    return from_cuda(transpose_dense<T>(rx, nrhs, static_cast<T *>(x), ld, n, nrhs, s));
+}
+}  // namespace
+
+extern "C" sptrsv_status sptrsv_solve_layout(sptrsv_plan p, const void *b, void *x, int32_t nrhs, int64_t ld,
+                                             int32_t layout, int32_t transpose)
+{
+    Range range("sptrsv_solve_layout");
+    if (!p || p->batched || (layout != SPTRSV_ROW_MAJOR && layout != SPTRSV_COL_MAJOR)) return SPTRSV_EINVAL;
+    const bool tr = transpose != 0;
+    if (layout == SPTRSV_ROW_MAJOR || nrhs == 1) {
+        // one column: both layouts are the same vector
+        const int64_t ldr = layout == SPTRSV_ROW_MAJOR ? ld : 1;
+        if (layout == SPTRSV_COL_MAJOR && ld < p->M.L.n) return SPTRSV_EINVAL;
+        return p->dtype == SPTRSV_F64 ? solve_impl<double>(p, b, x, nrhs, ldr, tr)
+                                      : solve_impl<float>(p, b, x, nrhs, ldr, tr);
+    }
+    if (p->M.L.n == 0) return SPTRSV_OK;
+    if (!b || !x || nrhs < 1 || ld < p->M.L.n) return SPTRSV_EINVAL;
+    if (tr && !p->have_csc) return SPTRSV_ENOTSUP;
+    return p->dtype == SPTRSV_F64 ? solve_colmajor<double>(p, b, x, nrhs, ld, tr)
+                                  : solve_colmajor<float>(p, b, x, nrhs, ld, tr);
+}
+
 extern "C" sptrsv_status sptrsv_grad_vals(sptrsv_plan p, const void *gb, const void *x, int32_t nrhs,
                                           int64_t ld, void *gvals)
 {
@@ -779,9 +834,9 @@ extern "C" sptrsv_status sptrsv_grad_vals(sptrsv_plan p, const void *gb, const v
     if (!gb || !x || !gvals || nrhs < 1 || ld < nrhs) return SPTRSV_EINVAL;
     cudaError_t e;
     if (p->dtype == SPTRSV_F64)
-        e = grad_vals<double>(sys_of<double>(p->M), (const double *)gb, (const double *)x, ld, nrhs, (double *)gvals, p->h->stream);
+        e = grad_vals<double>(sys_of<double>(p->M, p->h->d_status), (const double *)gb, (const double *)x, ld, nrhs, (double *)gvals, p->h->stream);
     else
-        e = grad_vals<float>(sys_of<float>(p->M), (const float *)gb, (const float *)x, ld, nrhs, (float *)gvals, p->h->stream);
+        e = grad_vals<float>(sys_of<float>(p->M, p->h->d_status), (const float *)gb, (const float *)x, ld, nrhs, (float *)gvals, p->h->stream);
     return from_cuda(e);
 }
 
@@ -793,9 +848,9 @@ extern "C" sptrsv_status sptrsv_tt_apply(sptrsv_plan p, const void *gbp, void *g
     if (!gbp || !gb || nrhs < 1 || ld < nrhs) return SPTRSV_EINVAL;
     cudaError_t e;
     if (p->dtype == SPTRSV_F64)
-        e = tt_apply<double>(sys_of<double>(p->M), (const double *)gbp, (double *)gb, ld, nrhs, p->h->stream);
+        e = tt_apply<double>(sys_of<double>(p->M, p->h->d_status), (const double *)gbp, (double *)gb, ld, nrhs, p->h->stream);
     else
-        e = tt_apply<float>(sys_of<float>(p->M), (const float *)gbp, (float *)gb, ld, nrhs, p->h->stream);
+        e = tt_apply<float>(sys_of<float>(p->M, p->h->d_status), (const float *)gbp, (float *)gb, ld, nrhs, p->h->stream);
     return from_cuda(e);
 }
 
@@ -1326,4 +1381,29 @@ extern "C" sptrsv_status sptrsv_batch_step_wait(sptrsv_plan p)
     e = cudaMemcpy(&status, p->h->d_status, sizeof(int), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return from_cuda(e);
     return (sptrsv_status)status;
+}
+
+// ------------------------------------------------------------ bounds checks
+namespace {
+__global__ void k_debug_check_index(int32_t index, int32_t n, int *status, int *out)
+{
+    const int v = chk_index(index, 0, n, status);
+    if (v >= 0 && v < n) out[0] = v;  // the access a checked index feeds
+}
+}  // namespace
+
+extern "C" int32_t sptrsv_checked_build(void)
+{
+#ifdef SPTRSV_CHECKED
+    return 1;
+#else
+    return 0;
+#endif
+}
+
+extern "C" sptrsv_status sptrsv_debug_check_index(sptrsv_handle h, int32_t index, int32_t n)
+{
+    if (!h || n < 1 || n > 32) return SPTRSV_EINVAL;
+    k_debug_check_index<<<1, 1, 0, h->stream>>>(index, n, h->d_status, reinterpret_cast<int *>(h->d_scratch));
+    return from_cuda(cudaGetLastError());
 }

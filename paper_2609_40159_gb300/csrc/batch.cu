@@ -22,6 +22,8 @@ __device__ __forceinline__ Sys<T> sys_of(const BatchMat &M)
     A.cp = M.cp; A.crow = M.crow; A.tmap = M.tmap; A.cv = (const T *)M.cv;
     A.trp = M.trp; A.tci = M.tci; A.tv = (const T *)M.tv; A.tmask = M.tmask;
     A.tcp = M.tcp; A.trow = M.trow; A.ttmap = M.ttmap;
+    A.nnz = M.nnz;
+    A.chk = nullptr;
     return A;
 }
 
@@ -34,6 +36,7 @@ __device__ __forceinline__ bool run_one(const BatchMat &M, const BatchItem &I, u
     reset_block_smem<T, KT>(sm, ring, I.kc);
     __syncthreads();
     Sys<T> A = sys_of<T>(M);
+    A.chk = w.status;
     // a rewritten system's forward right-hand side b + T b was formed by the
     // fold launch before this one (bt); the solve itself reads no T
     const bool folded = !TR && bt != nullptr && M.tmask != nullptr;

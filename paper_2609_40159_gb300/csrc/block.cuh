@@ -81,7 +81,7 @@ __device__ bool block_solve(const Sys<T> &A, const Rhs<T> &R, int rpw, int kc, i
             const int tb = A.trp[i], te = A.trp[i + 1];
             for (int p = tb + sl; p < te; p += lpr) {
                 const T tv = ldro(A.tv + p);
-                const T *bb = R.b + (int64_t)ldro(A.tci + p) * R.ld;
+                const T *bb = R.b + (int64_t)tcol(A, p) * R.ld;
 #pragma unroll
                 for (int r = 0; r < KT; ++r)
                     if (r < kt) acc[r] -= tv * bb[r];
@@ -322,7 +322,7 @@ __device__ bool block_solve_sweep(const Sys<T> &A, const Rhs<T> &R, int kc, int 
         if (!TR && valid && has_trow(A, i)) {
             for (int p = A.trp[i]; p < A.trp[i + 1]; ++p) {
                 const T tv = ldro(A.tv + p);
-                const T *bb = R.b + (int64_t)ldro(A.tci + p) * R.ld;
+                const T *bb = R.b + (int64_t)tcol(A, p) * R.ld;
 #pragma unroll
                 for (int r = 0; r < KT; ++r)
                     if (r < kt) acc[r] -= tv * bb[r];
@@ -560,9 +560,9 @@ __device__ bool block_solve_levels(const Sys<T> &A, const Rhs<T> &R, const int32
     const int kt = R.k;
     const T *ring0 = const_cast<const T *>(sm.xr);
     // row at processing position q; processing position of row j
-    auto row_at = [&](int q) { return ldro(perm + (TR ? n - 1 - q : q)); };
+    auto row_at = [&](int q) { return chk_row(A, ldro(perm + (TR ? n - 1 - q : q))); };
     auto pos_of = [&](int j) {
-        const int p = ldro(iperm + j);
+        const int p = chk_index(ldro(iperm + j), 0, n, A.chk);
         return TR ? n - 1 - p : p;
     };
     // a warp's next group, its rows and their extents are loaded one group
@@ -602,7 +602,7 @@ __device__ bool block_solve_levels(const Sys<T> &A, const Rhs<T> &R, const int32
         if (!TR && valid && has_trow(A, i)) {
             for (int p = A.trp[i]; p < A.trp[i + 1]; ++p) {
                 const T tv = ldro(A.tv + p);
-                const T *bb = R.b + (int64_t)ldro(A.tci + p) * R.ld;
+                const T *bb = R.b + (int64_t)tcol(A, p) * R.ld;
 #pragma unroll
                 for (int r = 0; r < KT; ++r)
                     if (r < kt) acc[r] -= tv * bb[r];

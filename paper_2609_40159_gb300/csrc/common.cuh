@@ -17,6 +17,25 @@ __device__ __forceinline__ void set_status(int *status, int code)
     atomicCAS(status, 0, code);
 }
 
+// ------------------------------------------------------------ bounds checks
+// SPTRSV_CHECKED builds (a debug variant of the library, the stand-in for a
+// memory checker): every index a solve gathers through must lie in
+// [lo, hi); one outside is recorded as SPTRSV_ERANGE in the status word
+// (when the kernel has one) and replaced by lo, so that the access it feeds
+// stays inside its array.  The product build compiles the identity.
+__device__ __forceinline__ int chk_index(int v, int lo, int hi, int *status)
+{
+#ifdef SPTRSV_CHECKED
+    if (v < lo || v >= hi) {
+        if (status) set_status(status, SPTRSV_ERANGE);
+        return lo;
+    }
+#else
+    (void)lo; (void)hi; (void)status;
+#endif
+    return v;
+}
+
 // -------------------------------------------------- memory-model primitives
 // Ready flags are published with st.release.gpu after the solution values and
 // polled with ld.acquire.gpu before the values are read (PTX memory model:

@@ -10,21 +10,37 @@ namespace spt {
 // ------------------------------------------------------------- row views
 template <class T, bool TR> struct RV;
 
+// (chk_*: identity in the product build, bounds checks in SPTRSV_CHECKED)
+template <class T> __device__ __forceinline__ int chk_row(const Sys<T> &A, int i)
+{
+    return chk_index(i, 0, A.n, A.chk);
+}
+template <class T> __device__ __forceinline__ int chk_pos(const Sys<T> &A, int p)
+{
+    return chk_index(p, 0, (int)A.nnz, A.chk);
+}
+
 template <class T> struct RV<T, false> {
-    static __device__ __forceinline__ int beg(const Sys<T> &A, int i) { return ldro(A.rp + i); }
-    static __device__ __forceinline__ int end(const Sys<T> &A, int i) { return ldro(A.rp + i + 1) - 1; }
-    static __device__ __forceinline__ T diag(const Sys<T> &A, int, int e) { return ldro(A.v + e); }
-    static __device__ __forceinline__ int col(const Sys<T> &A, int p) { return ldro(A.ci + p); }
-    static __device__ __forceinline__ T val(const Sys<T> &A, int p) { return ldro(A.v + p); }
+    static __device__ __forceinline__ int beg(const Sys<T> &A, int i) { return ldro(A.rp + chk_row(A, i)); }
+    static __device__ __forceinline__ int end(const Sys<T> &A, int i) { return ldro(A.rp + chk_row(A, i) + 1) - 1; }
+    static __device__ __forceinline__ T diag(const Sys<T> &A, int, int e) { return ldro(A.v + chk_pos(A, e)); }
+    static __device__ __forceinline__ int col(const Sys<T> &A, int p) { return chk_row(A, ldro(A.ci + chk_pos(A, p))); }
+    static __device__ __forceinline__ T val(const Sys<T> &A, int p) { return ldro(A.v + chk_pos(A, p)); }
 };
 
 template <class T> struct RV<T, true> {
-    static __device__ __forceinline__ int beg(const Sys<T> &A, int i) { return ldro(A.cp + i) + 1; }
-    static __device__ __forceinline__ int end(const Sys<T> &A, int i) { return ldro(A.cp + i + 1); }
-    static __device__ __forceinline__ T diag(const Sys<T> &A, int b, int) { return ldro(A.cv + b - 1); }
-    static __device__ __forceinline__ int col(const Sys<T> &A, int q) { return ldro(A.crow + q); }
-    static __device__ __forceinline__ T val(const Sys<T> &A, int q) { return ldro(A.cv + q); }
+    static __device__ __forceinline__ int beg(const Sys<T> &A, int i) { return ldro(A.cp + chk_row(A, i)) + 1; }
+    static __device__ __forceinline__ int end(const Sys<T> &A, int i) { return ldro(A.cp + chk_row(A, i) + 1); }
+    static __device__ __forceinline__ T diag(const Sys<T> &A, int b, int) { return ldro(A.cv + chk_pos(A, b - 1)); }
+    static __device__ __forceinline__ int col(const Sys<T> &A, int q) { return chk_row(A, ldro(A.crow + chk_pos(A, q))); }
+    static __device__ __forceinline__ T val(const Sys<T> &A, int q) { return ldro(A.cv + chk_pos(A, q)); }
 };
+
+// Column of entry p of T (the rewritten right-hand side's extra terms).
+template <class T> __device__ __forceinline__ int tcol(const Sys<T> &A, int p)
+{
+    return chk_row(A, ldro(A.tci + p));
+}
 
 template <class T>
 __device__ __forceinline__ bool has_trow(const Sys<T> &A, int i)

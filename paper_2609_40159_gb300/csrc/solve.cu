@@ -48,7 +48,7 @@ __global__ void k_level_launch(Sys<T> A, const int32_t *__restrict__ perm, int32
 {
     const int q = q_lo + blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= q_hi) return;
-    const int i = perm[q];
+    const int i = chk_row(A, perm[q]);
     const int a = RV<T, TR>::beg(A, i), e = RV<T, TR>::end(A, i);
     const T d = RV<T, TR>::diag(A, a, e);
     const bool ht = !TR && has_trow(A, i);
@@ -56,7 +56,7 @@ __global__ void k_level_launch(Sys<T> A, const int32_t *__restrict__ perm, int32
         T s = R.b[(int64_t)i * R.ld + r];
         if (ht)
             for (int p = A.trp[i]; p < A.trp[i + 1]; ++p)
-                s += A.tv[p] * R.b[(int64_t)A.tci[p] * R.ld + r];
+                s += A.tv[p] * R.b[(int64_t)tcol(A, p) * R.ld + r];
         for (int p = a; p < e; ++p)
             s -= RV<T, TR>::val(A, p) * R.x[(int64_t)RV<T, TR>::col(A, p) * R.ld + r];
         R.x[(int64_t)i * R.ld + r] = s / d;
@@ -90,7 +90,7 @@ __device__ __forceinline__ void gather_row(const Sys<T> &A, const Rhs<T> &R, int
         const int tb = A.trp[i], te = A.trp[i + 1];
         for (int p = tb + sl; p < te; p += lpr) {
             const T tv = ldro(A.tv + p);
-            const T *bb = R.b + (int64_t)ldro(A.tci + p) * R.ld + r0;
+            const T *bb = R.b + (int64_t)tcol(A, p) * R.ld + r0;
 #pragma unroll
             for (int r = 0; r < KT; ++r)
                 if (r < kt) acc[r] -= tv * bb[r];
@@ -117,7 +117,7 @@ __device__ __forceinline__ bool gather_row_run(const Sys<T> &A, const Rhs<T> &R,
         const int tb = A.trp[i], te = A.trp[i + 1];
         for (int p = tb + sl; p < te; p += lpr) {
             const T tv = ldro(A.tv + p);
-            const T *bb = R.b + (int64_t)ldro(A.tci + p) * R.ld + r0;
+            const T *bb = R.b + (int64_t)tcol(A, p) * R.ld + r0;
 #pragma unroll
             for (int r = 0; r < KT; ++r)
                 if (r < kt) acc[r] -= tv * bb[r];
@@ -125,7 +125,7 @@ __device__ __forceinline__ bool gather_row_run(const Sys<T> &A, const Rhs<T> &R,
     }
     for (int p = a + sl; p < e; p += lpr) {
         const int j = RV<T, TR>::col(A, p);
-        const int lj = ldro(S.lev + j);
+        const int lj = chk_index(ldro(S.lev + j), 0, S.nlevels, A.chk);
         if ((TR ? S.nlevels - 1 - lj : lj) >= h && !wait_flag(sy.flags + j, epoch, sy.w)) return false;
         const T vv = RV<T, TR>::val(A, p);
         const T *xx = R.x + (int64_t)j * R.ld + r0;
@@ -169,7 +169,7 @@ k_level_persistent(Sys<T> A, Sched S, Rhs<T> R, int rpw, SyncArgs sy)
             // solution: load them before waiting for the previous levels
             const int q = q0 + g;
             const bool active = q >= lo && q < hi;
-            const int i = active ? (TR ? S.perm[n - 1 - q] : S.perm[q]) : 0;
+            const int i = active ? chk_row(A, TR ? S.perm[n - 1 - q] : S.perm[q]) : 0;
             const int a = active ? RV<T, TR>::beg(A, i) : 0;
             const int e = active ? RV<T, TR>::end(A, i) : 0;
             const T rinv = active ? T(1) / RV<T, TR>::diag(A, a, e) : T(0);
@@ -259,7 +259,7 @@ k_syncfree(Sys<T> A, Rhs<T> R, int rpw, SyncArgs sy)
                 const int tb = A.trp[i], te = A.trp[i + 1];
                 for (int p = tb + sl; p < te; p += lpr) {
                     const T tv = ldro(A.tv + p);
-                    const T *bb = R.b + (int64_t)ldro(A.tci + p) * R.ld + r0;
+                    const T *bb = R.b + (int64_t)tcol(A, p) * R.ld + r0;
 #pragma unroll
                     for (int r = 0; r < KT; ++r)
                         if (r < kt) acc[r] -= tv * bb[r];
@@ -369,7 +369,7 @@ k_syncfree_sweep(Sys<T> A, Rhs<T> R, SyncArgs sy)
             if (!TR && valid && has_trow(A, i)) {
                 for (int p = A.trp[i]; p < A.trp[i + 1]; ++p) {
                     const T tv = ldro(A.tv + p);
-                    const T *bb = R.b + (int64_t)ldro(A.tci + p) * R.ld + r0;
+                    const T *bb = R.b + (int64_t)tcol(A, p) * R.ld + r0;
 #pragma unroll
                     for (int r = 0; r < KT; ++r)
                         if (r < ktile) acc[r] -= tv * bb[r];
@@ -740,6 +740,40 @@ int persistent_grid_syncfree(int kt, bool f64, const DeviceInfo &di)
     return per_sm * di.num_sms;
 }
 
+// ------------------------------------------------------ dense layouts
+template <class T>
+__global__ void __launch_bounds__(256)
+k_transpose_dense(const T *__restrict__ src, int64_t lds, T *__restrict__ dst, int64_t ldd, int64_t rows,
+                  int64_t cols)
+{
+    __shared__ T tile[32][33];
+    const int64_t tr = (rows + 31) / 32, tc = (cols + 31) / 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8 threads
+    for (int64_t t = blockIdx.x; t < tr * tc; t += gridDim.x) {
+        const int64_t r0 = (t / tc) * 32, c0 = (t % tc) * 32;
+        for (int y = ty; y < 32; y += 8) {
+            const int64_t r = r0 + y, c = c0 + tx;
+            if (r < rows && c < cols) tile[y][tx] = src[r * lds + c];
+        }
+        __syncthreads();
+        for (int y = ty; y < 32; y += 8) {
+            const int64_t c = c0 + y, r = r0 + tx;
+            if (r < rows && c < cols) dst[c * ldd + r] = tile[tx][y];
+        }
+        __syncthreads();
+    }
+}
+
+template <class T>
+cudaError_t transpose_dense(const T *src, int64_t lds, T *dst, int64_t ldd, int64_t rows, int64_t cols,
+                            cudaStream_t s)
+{
+    if (rows <= 0 || cols <= 0) return cudaSuccess;
+    const int64_t tiles = ((rows + 31) / 32) * ((cols + 31) / 32);
+    k_transpose_dense<T><<<(int)std::min<int64_t>(tiles, 152 * 16), 256, 0, s>>>(src, lds, dst, ldd, rows, cols);
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------ CSC values
 template <class T>
 __global__ void k_csc_values(const int32_t *__restrict__ tmap, const T *__restrict__ v, T *__restrict__ cv,
@@ -774,7 +808,8 @@ cudaError_t csc_values(const int32_t *tmap, const T *v, T *cv, int64_t nnz, cuda
     template cudaError_t grad_vals<T>(const Sys<T> &, const T *, const T *, int64_t, int32_t, T *,      \
                                       cudaStream_t);                                                    \
     template cudaError_t tt_apply<T>(const Sys<T> &, const T *, T *, int64_t, int32_t, cudaStream_t);   \
-    template cudaError_t csc_values<T>(const int32_t *, const T *, T *, int64_t, cudaStream_t);
+    template cudaError_t csc_values<T>(const int32_t *, const T *, T *, int64_t, cudaStream_t);          \
+    template cudaError_t transpose_dense<T>(const T *, int64_t, T *, int64_t, int64_t, int64_t, cudaStream_t);
 SPT_INST(double)
 SPT_INST(float)
 #undef SPT_INST

@@ -25,6 +25,8 @@ template <class T> struct Sys {
     const int32_t *tcp;     // CSC of T (adjoint of b + T b): column pointers,
     const int32_t *trow;    //   row of every CSC entry (ascending),
     const int32_t *ttmap;   //   CSR position of every CSC entry
+    int64_t nnz;            // entries of L (bounds of the checked build)
+    int *chk;               // status word of the checked build's bounds checks
 };
 
 // Level schedule.
@@ -219,6 +221,11 @@ template <class T>
 cudaError_t batch_tt_apply(const BatchMat *mats, const RowChunk *tchunks, int64_t ntchunks,
                            int64_t total_rhs, const T *gbp, T *gb, cudaStream_t s);
 int batch_grid(size_t smem, const DeviceInfo &di);
+// dst[c * ldd + r] = src[r * lds + c] for r < rows, c < cols (32 x 32
+// tiles through shared memory: both sides read and written along rows).
+template <class T>
+cudaError_t transpose_dense(const T *src, int64_t lds, T *dst, int64_t ldd, int64_t rows, int64_t cols,
+                            cudaStream_t s);
 // iperm[perm[q]] = q for q < n.
 cudaError_t inverse_perm(const int32_t *perm, int32_t *iperm, int32_t n, cudaStream_t s);
 

@@ -41,6 +41,19 @@ def test_binding_declares_same_names(lib_path):
     assert lib.sptrsv_status_string(0) == b"ok"
 
 
+def test_checked_variant_exports_the_same_abi(lib_path):
+    """The bounds-checked debug variant (SPTRSV_CHECKED) is built beside the
+    product library, exports the same entry points and says which it is."""
+    from paper_2609_40159_gb300 import _lib
+    assert os.path.exists(_lib.LIB_CHECKED_PATH)
+    out = subprocess.run(["nm", "-D", "--defined-only", _lib.LIB_CHECKED_PATH], capture_output=True, text=True,
+                         check=True).stdout
+    exported = sorted({ln.split()[-1] for ln in out.splitlines() if ln.split()[-1].startswith("sptrsv_")})
+    assert exported == _declared()
+    assert _lib.load(_lib.LIB_CHECKED_PATH).sptrsv_checked_build() == 1
+    assert _lib.load(lib_path).sptrsv_checked_build() == 0
+
+
 def test_missing_library_fails_loudly(tmp_path):
     from paper_2609_40159_gb300 import _lib
     with pytest.raises(OSError, match="no CPU fallback"):

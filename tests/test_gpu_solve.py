@@ -269,6 +269,32 @@ def test_hybrid_thin_thresholds(name):
     assert P.handle().status() == 0
 
 
+@pytest.mark.parametrize("mode", ["level", "syncfree", "block", "hybrid"])
+def test_column_major_multi_rhs(mode):
+    """SpTRSM in the column-major layout (every right-hand side contiguous,
+    padded leading dimension too): forward and transpose vs the oracle, and
+    equal to the row-major solve of the same block; 1 and 13 right-hand
+    sides; a wider block later regrows the plan's buffer."""
+    import paper_2609_40159_gb300 as P
+    A_h = S.band_random(7001, 96, 1, 12, seed=21)
+    A = P.Matrix.from_host(A_h)
+    plan = P.Plan(A, mode=mode, transpose=True)
+    for k, pad in ((13, 0), (1, 0), (13, 77), (40, 3)):
+        Bh = S.rhs(A_h.n, k, seed=k + pad)                   # [n, k]
+        store = torch.zeros(k, A_h.n + pad, dtype=torch.float64, device="cuda")
+        B = store[:, :A_h.n]
+        B.copy_(torch.as_tensor(Bh.T))
+        X = plan.solve_columns(B)
+        G = plan.solve_columns(B, transpose=True)
+        assert P.handle().status() == 0
+        assert relerr(X.cpu().numpy().T, oracle.solve(A_h, Bh)) <= 1e-12, (k, pad)
+        assert relerr(G.cpu().numpy().T, oracle.solve_transpose(A_h, Bh)) <= 1e-12, (k, pad)
+        Xr = plan.solve(torch.as_tensor(Bh).cuda())
+        assert relerr(X.cpu().numpy().T, Xr.cpu().numpy()) <= 1e-14, (k, pad)
+    with pytest.raises(P.SpTRSVError):
+        P._lib.check(P._lib.lib().sptrsv_solve_layout(plan.p, P.api._ptr(B), P.api._ptr(X), 40, 10, 1, 0))
+
+
 def test_cuda_graph_replay():
     import paper_2609_40159_gb300 as P
     A_h = S.band_random(50_000, 64, 4, 16, seed=11)
