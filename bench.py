@@ -62,8 +62,8 @@ def parse():
 
 def profile_single(N):
     """A small single-system case for a profiler: the kernels of the level
-    analysis, the level-persistent and the sync-free solve on the N x N 2D
-    Laplacian (2N-1 levels), each run 3 times after one warm-up."""
+    analysis, the level-persistent, the sync-free and the hybrid solve on the
+    N x N 2D Laplacian (2N-1 levels), each run 3 times after one warm-up."""
     import torch
     import paper_2609_40159_gb300 as P
     from paper_2609_40159_gb300 import autotune
@@ -73,8 +73,8 @@ def profile_single(N):
     out = {"n": A.n, "levels": 2 * N - 1}
     out["analyze_ms"] = autotune.time_call(lambda: P.analyze(A), reps=3, warmup=1)
     plan = P.Plan(A)
-    for mode in ("level", "syncfree"):
-        plan.set(mode, 32, 1)
+    for mode in ("level", "syncfree", "hybrid"):
+        plan.set(mode, 4 if mode == "hybrid" else 32, 1)
         ms = autotune.time_call(lambda: plan.solve(b, out=x), reps=3, warmup=1)
         out[mode] = {"ms": ms, "us_per_level": 1e3 * ms / (2 * N - 1)}
     if P.handle().status() != 0:
