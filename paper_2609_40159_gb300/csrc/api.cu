@@ -125,6 +125,9 @@ struct sptrsv_plan_st {
     int32_t *d_chunk_fwd = nullptr, *d_chunk_tr = nullptr;
     int chunk_rpw = 0;
     uint32_t *d_flags = nullptr;
+    // value-carrying ready flags of single-right-hand-side solves (16 bytes
+    // per row: the solution bits and the epoch)
+    unsigned long long *d_vflags = nullptr;
     int grid_level = 0, grid_sf = 0;
     int32_t max_width = 0;
     // hybrid schedule: thin-level threshold (0 = automatic) and, per
@@ -505,6 +508,9 @@ sptrsv_status solve_impl(sptrsv_plan p, const void *b, void *x, int32_t nrhs, in
         if (eg != cudaSuccess) return from_cuda(eg);
     }
     SyncArgs sy{p->d_flags, p->d_ctl, p->withhold, Waiter{p->h->d_status, &p->d_ctl->abort_flag, p->spin}};
+    // one right-hand side: the synchronisation-free waits read the values
+    // from the flags themselves
+    if (nrhs == 1) sy.vflags = p->d_vflags;
     const int kt = std::min(p->kt, default_kt(nrhs));
     cudaError_t e = cudaSuccess;
     int mode = p->mode;
@@ -666,6 +672,8 @@ extern "C" sptrsv_status sptrsv_plan_create(sptrsv_handle h, const sptrsv_csr *L
     if (e == cudaSuccess) e = cudaMemset(p->d_ctl, 0, sizeof(PlanCtl));
     if (e == cudaSuccess) e = p->alloc(&p->d_flags, sizeof(uint32_t) * (size_t)(L->n > 0 ? L->n : 1));
     if (e == cudaSuccess) e = cudaMemset(p->d_flags, 0, sizeof(uint32_t) * (size_t)(L->n > 0 ? L->n : 1));
+    if (e == cudaSuccess) e = p->alloc(&p->d_vflags, 16 * (size_t)(L->n > 0 ? L->n : 1));
+    if (e == cudaSuccess) e = cudaMemset(p->d_vflags, 0, 16 * (size_t)(L->n > 0 ? L->n : 1));
     if (e != cudaSuccess) { sptrsv_plan_destroy(p); return from_cuda(e); }
     st = prepare_mat(p, p->M, *L, T, o.build_transpose != 0);
     if (st != SPTRSV_OK) { sptrsv_plan_destroy(p); return st; }

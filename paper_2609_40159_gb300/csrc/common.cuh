@@ -236,6 +236,58 @@ __device__ __forceinline__ bool wait_count(const unsigned long long *counter,
     }
 }
 
+// ------------------------------------------------- value-carrying flags
+// With one right-hand side a row's ready flag can carry the row's solution:
+// the solve's epoch and the value's bits in one flag word, written once per
+// solve.  A waiter has the value as soon as it sees the flag (one L2 round
+// trip instead of two), and since nothing else is read through the flag,
+// relaxed accesses suffice: the producer needs no release fence.  FP32: one
+// 64-bit word {bits, epoch}.  FP64: two 64-bit halves {low bits, epoch} and
+// {high bits, epoch}, each checked on its own, so that only the per-half
+// single-copy atomicity of aligned 64-bit accesses is relied on.
+__device__ __forceinline__ void vflag_publish(unsigned long long *f, int64_t i, float x, uint32_t epoch)
+{
+    const unsigned long long v = ((unsigned long long)epoch << 32) | __float_as_uint(x);
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(f + i), "l"(v) : "memory");
+}
+__device__ __forceinline__ void vflag_publish(unsigned long long *f, int64_t i, double x, uint32_t epoch)
+{
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+    const unsigned long long lo = ((unsigned long long)epoch << 32) | (bits & 0xffffffffull);
+    const unsigned long long hi = ((unsigned long long)epoch << 32) | (bits >> 32);
+    asm volatile("st.relaxed.gpu.global.v2.u64 [%0], {%1, %2};" ::"l"(f + 2 * i), "l"(lo), "l"(hi) : "memory");
+}
+__device__ __forceinline__ bool vflag_try(const unsigned long long *f, int64_t j, uint32_t epoch, float &x)
+{
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(f + j) : "memory");
+    x = __uint_as_float((uint32_t)v);
+    return (uint32_t)(v >> 32) == epoch;
+}
+__device__ __forceinline__ bool vflag_try(const unsigned long long *f, int64_t j, uint32_t epoch, double &x)
+{
+    unsigned long long lo, hi;
+    asm volatile("ld.relaxed.gpu.global.v2.u64 {%0, %1}, [%2];" : "=l"(lo), "=l"(hi) : "l"(f + 2 * j) : "memory");
+    x = __longlong_as_double((long long)((hi << 32) | (lo & 0xffffffffull)));
+    return (uint32_t)(lo >> 32) == epoch && (uint32_t)(hi >> 32) == epoch;
+}
+
+// Wait until row j's value flag carries this solve's epoch; the value is
+// returned in x.  Returns false on timeout / abort.
+template <class T>
+__device__ __forceinline__ bool wait_value(const unsigned long long *f, int64_t j, uint32_t epoch,
+                                           const Waiter &w, T &x)
+{
+    if (vflag_try(f, j, epoch, x)) return true;
+    WaitClock clk;
+    Backoff bo;
+    for (;;) {
+        if (vflag_try(f, j, epoch, x)) return true;
+        if (clk.expired(w)) return false;
+        bo.pause();
+    }
+}
+
 // ------------------------------------------------------------------ warp ops
 template <class T> __device__ __forceinline__ T shfl_xor(T v, int m)
 {

@@ -126,8 +126,16 @@ __device__ __forceinline__ bool gather_row_run(const Sys<T> &A, const Rhs<T> &R,
     for (int p = a + sl; p < e; p += lpr) {
         const int j = RV<T, TR>::col(A, p);
         const int lj = chk_index(ldro(S.lev + j), 0, S.nlevels, A.chk);
-        if ((TR ? S.nlevels - 1 - lj : lj) >= h && !wait_flag(sy.flags + j, epoch, sy.w)) return false;
         const T vv = RV<T, TR>::val(A, p);
+        const bool in_run = (TR ? S.nlevels - 1 - lj : lj) >= h;
+        if (in_run && sy.vflags) {
+            // one right-hand side: the flag carries the value
+            T xv;
+            if (!wait_value(sy.vflags, j, epoch, sy.w, xv)) return false;
+            acc[0] += vv * xv;
+            continue;
+        }
+        if (in_run && !wait_flag(sy.flags + j, epoch, sy.w)) return false;
         const T *xx = R.x + (int64_t)j * R.ld + r0;
 #pragma unroll
         for (int r = 0; r < KT; ++r)
@@ -203,7 +211,12 @@ k_level_persistent(Sys<T> A, Sched S, Rhs<T> R, int rpw, SyncArgs sy)
                     for (int r = 0; r < KT; ++r)
                         if (r < kt) xx[r] = (bb[r] - acc[r]) * rinv;
                     // hybrid: the row's ready flag (after its last tile)
-                    if (S.seg && r0 + KT >= R.k && i != sy.withhold) st_release(sy.flags + i, epoch);
+                    if (S.seg && r0 + KT >= R.k && i != sy.withhold) {
+                        if (sy.vflags)
+                            vflag_publish(sy.vflags, i, (bb[0] - acc[0]) * rinv, epoch);
+                        else
+                            st_release(sy.flags + i, epoch);
+                    }
                 }
             }
             // test hook: a withheld row is never counted, so that every
@@ -281,6 +294,11 @@ k_syncfree(Sys<T> A, Rhs<T> R, int rpw, SyncArgs sy)
 #pragma unroll
                             for (int r = 0; r < KT; ++r)
                                 if (r < kt) acc[r] += vv * xs[gj * KT + r];
+                        } else if (sy.vflags) {
+                            // one right-hand side: the flag carries the value
+                            T xv;
+                            if (!wait_value(sy.vflags, j, epoch, sy.w, xv)) { failed = true; break; }
+                            acc[0] += vv * xv;
                         } else {
                             if (!wait_flag(sy.flags + j, epoch, sy.w)) { failed = true; break; }
                             const T *xx = R.x + (int64_t)j * R.ld + r0;
@@ -312,7 +330,12 @@ k_syncfree(Sys<T> A, Rhs<T> R, int rpw, SyncArgs sy)
                                 xs[g * KT + r] = xv;
                                 xx[r] = xv;
                             }
-                        if (last_tile && i != sy.withhold) st_release(sy.flags + i, epoch);
+                        if (last_tile && i != sy.withhold) {
+                            if (sy.vflags)
+                                vflag_publish(sy.vflags, i, (bb[0] - red[0]) / d, epoch);
+                            else
+                                st_release(sy.flags + i, epoch);
+                        }
                     }
                 }
                 fin |= __ballot_sync(SPT_FULL_MASK, newly && sl == 0);
@@ -400,6 +423,13 @@ k_syncfree_sweep(Sys<T> A, Rhs<T> R, SyncArgs sy)
                                 coef[(pj - base) * 32 + lane] = vvv[u];
                                 continue;
                             }
+                            if (sy.vflags) {
+                                // one right-hand side: the flag carries the value
+                                T xv;
+                                if (!wait_value(sy.vflags, j, epoch, sy.w, xv)) { failed = true; continue; }
+                                acc[0] += vvv[u] * xv;
+                                continue;
+                            }
                             if (!wait_flag(sy.flags + j, epoch, sy.w)) { failed = true; continue; }
                             const T *xx = R.x + (int64_t)j * R.ld + r0;
 #pragma unroll
@@ -415,7 +445,12 @@ k_syncfree_sweep(Sys<T> A, Rhs<T> R, SyncArgs sy)
 #pragma unroll
                 for (int r = 0; r < KT; ++r)
                     if (r < ktile) xx[r] = (bv[r] - acc[r]) * rinv;
-                if (last_tile && i != sy.withhold) st_release(sy.flags + i, epoch);
+                if (last_tile && i != sy.withhold) {
+                    if (sy.vflags)
+                        vflag_publish(sy.vflags, i, (bv[0] - acc[0]) * rinv, epoch);
+                    else
+                        st_release(sy.flags + i, epoch);
+                }
             }
             __syncwarp();
         }

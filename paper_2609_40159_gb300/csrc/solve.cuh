@@ -65,6 +65,9 @@ struct SyncArgs {
     PlanCtl *ctl;
     int32_t withhold;
     Waiter w;
+    // value-carrying flags (16 bytes per row), used instead of flags + x
+    // when the solve has one right-hand side; nullptr otherwise
+    unsigned long long *vflags = nullptr;
 };
 
 // ---------------------------------------------------------------- launchers
