@@ -41,6 +41,17 @@ WORKLOAD = ("batch512: 512 banded lower-triangular CSR systems, n~logU[1e3,2e5],
 FALLBACK_HBM = 6800.0
 
 
+def workload_name(args):
+    """The workload string of the JSON line (the benchmark's, unless the
+    batch was resized for a profiling run)."""
+    w = WORKLOAD
+    if args.nmat != 512:
+        w = w.replace("batch512: 512 ", f"batch{args.nmat}: {args.nmat} ")
+    if args.n_hi != 200_000:
+        w = w.replace("n~logU[1e3,2e5]", f"n~logU[1e3,{args.n_hi}]")
+    return w
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -48,6 +59,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--nmat", type=int, default=512)
+    ap.add_argument("--n-hi", type=int, default=200_000,
+                    help="largest system of the batch (rows); smaller values give a still contended "
+                         "batch small enough for a full profiler capture")
     ap.add_argument("--split", action="store_true",
                     help="split ONE batch over the ranks (shard.partition, strong scaling) instead of "
                          "one batch per rank (weak scaling)")
@@ -222,7 +236,7 @@ def run_reference(args, items, rank):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tt / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "reference": "CPU oracle (no reference code exists)"},
+        "config": {"workload": workload_name(args), "reference": "CPU oracle (no reference code exists)"},
         "cpu_baseline": {"kind": "oracle", "value": gbs, "unit": "GB/s", "cores": 1,
                          "sample": f"{per} of {nmat} systems per step (rotating), fwd + transpose "
                                    "solve + value gradient, FP64 on widened FP32 values"},
@@ -272,11 +286,11 @@ def main():
     # deterministic partition every rank computes alike
     if args.split:
         from paper_2609_40159_gb300 import shard
-        items = S.batch_spec_parallel(nmat=args.nmat, seed=3)
+        items = S.batch_spec_parallel(nmat=args.nmat, seed=3, n_hi=args.n_hi)
         costs = [shard.system_cost(it.A.n, it.A.nnz, it.nrhs) for it in items]
         items = [items[m] for m in shard.local_share(costs, rank, world)]
     else:
-        items = S.batch_spec_parallel(nmat=args.nmat, seed=3 + 1000 * rank)
+        items = S.batch_spec_parallel(nmat=args.nmat, seed=3 + 1000 * rank, n_hi=args.n_hi)
     if args.impl == "reference":
         if rank == 0:
             run_reference(args, items, rank)
@@ -491,7 +505,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
             "scaling": "strong" if args.split else "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "systems_per_gpu": len(items),
+            "config": {"workload": workload_name(args), "systems_per_gpu": len(items),
                        "rows_per_gpu": int(sum(A.n for A in mats)),
                        "nnz_per_gpu": int(sum(A.nnz for A in mats)),
                        "rhs_per_gpu": int(sum(it.nrhs * it.A.n for it in items)),
