@@ -73,6 +73,19 @@ constexpr int kLevWarps = kLevThreads / 32;
 
 constexpr int kLevLong = 32;  // rows with more off-diagonals are walked by the whole warp
 
+// Levels by a synchronisation-free pass over chunks of 32 consecutive rows,
+// taken by warps from a ticket: a chunk only waits on chunks already taken
+// by running warps, so the pass needs no co-residency.  A level is its own
+// ready flag (-1 until published, read with relaxed loads).  A chunk works
+// in rounds: every row polls its dependencies on earlier chunks without
+// blocking (a cursor stops at the first one not yet published); a row
+// whose earlier-chunk dependencies are all seen and whose dependencies in
+// the chunk are all published takes its level at once (the chunk's levels
+// are kept in shared memory), so that rows are published as early as
+// their own dependencies allow.  Once every row has seen all of its
+// earlier-chunk dependencies, the rows left (chains inside the chunk) are
+// resolved together by a 31-step shuffle sweep instead of one row per
+// round.  The polls are bounded in time.
 __global__ void __launch_bounds__(kLevThreads)
 k_levels(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, int32_t n, int32_t *lev,
          unsigned long long *ticket, Waiter w, int32_t withhold)
@@ -89,95 +102,91 @@ k_levels(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, int32_t
         const int64_t i = base + lane;
         const bool valid = i < n;
         const int a = valid ? ldro(rp + i) : 0;
-        int p = a;
         const int pend = valid ? ldro(rp + i + 1) - 1 : 0;
-        // long rows are left to the cooperative step below
+        // long rows are polled by the whole warp (below)
         const bool islong = pend - a > kLevLong;
-        int m = -1;
-        bool done = !valid, failed = false;
-        my[lane] = -1;
-        __syncwarp();
-        WaitClock stall;  // bounds rounds in which no row of the chunk completes
+        int p = a;              // next entry of this row to look at
+        int m = -1;             // deepest earlier-chunk dependency seen
+        unsigned dmask = 0;     // dependencies on rows of this chunk
+        bool ext = !valid || (!islong && a >= pend);  // every earlier-chunk dependency seen
+        bool pub = !valid;      // level published (or withheld by the test hook)
+        WaitClock clk;
         for (;;) {
-            const unsigned done_before = __ballot_sync(SPT_FULL_MASK, done);
-            if (!done && !islong) {
-                while (p < pend) {
-                    const int32_t j = ldro(ci + p);
-                    int lj;
-                    if (j >= base) {
-                        lj = my[j - base];
-                        if (lj < 0) break;  // produced by this warp later
-                    } else {
-                        lj = ld_relaxed(lev + j);
-                        if (lj < 0) {
-                            WaitClock clk;
-                            for (;;) {
-                                lj = ld_relaxed(lev + j);
-                                if (lj >= 0) break;
-                                if (clk.expired(w)) { failed = true; break; }
-                            }
-                            if (failed) break;
-                        }
-                    }
+            bool moved = false;
+            // ---- 1. earlier-chunk dependencies, without blocking
+            while (!ext && !islong && p < pend) {
+                const int32_t j = ldro(ci + p);
+                if (j >= base) {
+                    dmask |= 1u << (j - base);
+                } else {
+                    const int lj = ld_relaxed(lev + j);
+                    if (lj < 0) break;
                     m = m > lj ? m : lj;
-                    ++p;
                 }
-                if (failed) done = true;
-                else if (p >= pend) {
-                    const int lv = m + 1;
-                    my[lane] = lv;
-                    if (i != withhold) st_relaxed(lev + i, lv);  // test hook: never published
-                    done = true;
-                }
+                ++p;
+                moved = true;
             }
-            __syncwarp();
-            // cooperative step: the lowest pending long row, entries split
-            // over the lanes; retried later if one of them depends on a row
-            // of this chunk that is not done yet (a short row below it, which
-            // progresses, since every long row below it is done)
-            const unsigned pending = __ballot_sync(SPT_FULL_MASK, islong && !done);
-            if (pending) {
+            if (!islong && p >= pend) ext = true;
+            unsigned pending = __ballot_sync(SPT_FULL_MASK, islong && !ext);
+            while (pending) {
                 const int s = __ffs(pending) - 1;
+                pending &= pending - 1;
                 const int sa = __shfl_sync(SPT_FULL_MASK, a, s);
                 const int se = __shfl_sync(SPT_FULL_MASK, pend, s);
                 int ms = -1;
-                bool blocked = false;
-                for (int q = sa + lane; q < se && !blocked && !failed; q += 32) {
+                unsigned dm = 0;
+                bool wait = false;
+                for (int q = sa + lane; q < se; q += 32) {
                     const int32_t j = ldro(ci + q);
-                    int lj;
                     if (j >= base) {
-                        lj = my[j - base];
-                        if (lj < 0) blocked = true;
+                        dm |= 1u << (j - base);
                     } else {
-                        lj = ld_relaxed(lev + j);
-                        if (lj < 0) {
-                            WaitClock clk;
-                            for (;;) {
-                                lj = ld_relaxed(lev + j);
-                                if (lj >= 0) break;
-                                if (clk.expired(w)) { failed = true; break; }
-                            }
-                        }
+                        const int lj = ld_relaxed(lev + j);
+                        wait |= lj < 0;
+                        ms = ms > lj ? ms : lj;
                     }
-                    ms = ms > lj ? ms : lj;
                 }
-                const bool any_blocked = __any_sync(SPT_FULL_MASK, blocked);
-                const bool any_failed = __any_sync(SPT_FULL_MASK, failed);
-                const int mx = __reduce_max_sync(SPT_FULL_MASK, ms);
-                if (!any_blocked && !any_failed && lane == s) {
-                    my[lane] = mx + 1;
-                    if (i != withhold) st_relaxed(lev + i, mx + 1);
-                    done = true;
+                ms = __reduce_max_sync(SPT_FULL_MASK, ms);
+                dm = __reduce_or_sync(SPT_FULL_MASK, dm);
+                if (!__any_sync(SPT_FULL_MASK, wait) && lane == s) {
+                    m = ms;
+                    dmask = dm;
+                    ext = true;
+                    moved = true;
                 }
-                __syncwarp();
             }
-            if (__any_sync(SPT_FULL_MASK, failed)) return;
-            const unsigned done_after = __ballot_sync(SPT_FULL_MASK, done);
-            if (done_after == SPT_FULL_MASK) break;
-            // every round completes a row (the lowest unfinished row of the
-            // chunk has all its in-chunk dependencies done); the bound only
-            // guards that argument
-            if (done_after == done_before && stall.expired(w)) return;
+            // ---- 2. rows whose dependencies in the chunk are all published
+            const unsigned pubm = __ballot_sync(SPT_FULL_MASK, pub);
+            if (ext && !pub && (dmask & ~pubm) == 0) {
+                int lv = m + 1;
+                for (unsigned bits = dmask; bits; bits &= bits - 1) {
+                    const int ls = my[__ffs(bits) - 1] + 1;
+                    lv = lv > ls ? lv : ls;
+                }
+                my[lane] = lv;
+                if (i != withhold) st_relaxed(lev + i, lv);  // test hook: never published
+                pub = true;
+                moved = true;
+            }
+            __syncwarp();
+            if (__all_sync(SPT_FULL_MASK, pub)) break;
+            // ---- 3. every earlier-chunk dependency seen: the rows left are
+            // chains inside the chunk, resolved by one max-plus sweep (step s
+            // broadcasts row s's level, final as all of its dependencies are
+            // earlier rows; every row depending on it takes it + 1)
+            if (__all_sync(SPT_FULL_MASK, ext)) {
+                int lv = pub ? my[lane] : m + 1;
+#pragma unroll
+                for (int s = 0; s < 31; ++s) {
+                    const int ls = __shfl_sync(SPT_FULL_MASK, lv, s) + 1;
+                    if ((dmask >> s) & 1u) lv = lv > ls ? lv : ls;
+                }
+                if (!pub && i != withhold) st_relaxed(lev + i, lv);
+                break;
+            }
+            // one decision for the whole warp (the lanes' clocks may straddle
+            // the limit)
+            if (!__any_sync(SPT_FULL_MASK, moved) && __any_sync(SPT_FULL_MASK, clk.expired(w))) return;
         }
     }
 }
