@@ -34,6 +34,16 @@ def test_analyze_fp32_same_as_fp64():
     _check(S.band_random(5000, 100, 4, 16, seed=9).astype(np.float32))
 
 
+def test_analyze_long_rows_with_chains_in_chunk():
+    """Rows longer than the cooperative threshold (up to 40 off-diagonals in a
+    band of 48) that depend on rows of their own 32-row chunk as well as on
+    earlier chunks, mixed with short rows: the warp-wide polls, the
+    per-row early publishing and the chunk's max-plus sweep together, vs the
+    oracle."""
+    _check(S.band_random(20_000, 48, 20, 40, seed=13))
+    _check(S.band_random(9_001, 40, 0, 39, seed=14))
+
+
 def test_analysis_bounded_wait_reports_timeout():
     """A row whose level is never published (test hook): the level analysis
     gives up after the hook's wait limit with SPTRSV_ETIMEOUT (returned by
