@@ -197,16 +197,17 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity, const 
     }
 }
 
-// Global-memory polls back off exponentially (__nanosleep, 32 ns .. 512 ns)
-// so that thousands of waiting warps do not saturate the L2 slice that holds
-// the flag the producer is about to write.
+// Global-memory polls sleep 32 ns between attempts, so that thousands of
+// waiting warps leave issue slots and L2 bandwidth to the producers.  The
+// sleep is not lengthened.  Measured against a sleep doubling up to 512 ns:
+// with value-carrying flags a hop is one L2 round trip, and the longer
+// sleeps added their length to the hops of the hybrid solve, the automatic
+// choice for such systems (lap2d 1024^2 FP64 4.24 -> 3.2 ms, power-law
+// 116 -> 82 ms); the row-order synchronisation-free and level-persistent
+// modes, whose waiters sit far ahead of the wavefront, lose about 20 % on
+// the power-law DAG with the short sleep and gain a little on lap2d.
 struct Backoff {
-    unsigned ns = 32;
-    __device__ __forceinline__ void pause()
-    {
-        __nanosleep(ns);
-        if (ns < 512) ns <<= 1;
-    }
+    __device__ __forceinline__ void pause() { __nanosleep(32); }
 };
 
 // Wait until flag == want.  Returns false on timeout / abort.
