@@ -291,6 +291,13 @@ sptrsv_status sptrsv_batch_offsets(sptrsv_plan plan, int64_t *rhs_offset, int64_
  * Returns SPTRSV_EINVAL for a negative value or a batched plan.
  * Synchronises.                                                           */
 sptrsv_status sptrsv_plan_set_thin_rows(sptrsv_plan plan, int32_t thin_rows);
+/* Resident thread blocks per SM of the level-persistent and hybrid solves'
+ * persistent grids (256 threads each): 0 = as many as fit (the default);
+ * otherwise at most that many.  Their waiting warps poll global memory, so
+ * fewer of them can be faster.  Any value is correct: a row group only
+ * waits on groups taken before it.  Returns SPTRSV_EINVAL for a negative
+ * value or a batched plan.                                                */
+sptrsv_status sptrsv_plan_set_blocks_per_sm(sptrsv_plan plan, int32_t blocks_per_sm);
 
 /* Re-tunes a batched plan (used by the autotuner; no analysis is repeated).
  *   rows_per_warp  host, nmat entries (1,2,4,8,16,32; 0 = keep) or NULL:

@@ -104,6 +104,7 @@ _SIGS = {
     "sptrsv_plan_info": [sptrsv_plan, _PI32, _PI32, _PI32, _PI32],
     "sptrsv_plan_set": [sptrsv_plan, _I32, _I32, _I32],
     "sptrsv_plan_set_thin_rows": [sptrsv_plan, _I32],
+    "sptrsv_plan_set_blocks_per_sm": [sptrsv_plan, _I32],
     "sptrsv_solve": [sptrsv_plan, _P, _P, _I32, _I64],
     "sptrsv_solve_transpose": [sptrsv_plan, _P, _P, _I32, _I64],
     "sptrsv_solve_layout": [sptrsv_plan, _P, _P, _I32, _I64, _I32, _I32],

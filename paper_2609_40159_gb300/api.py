@@ -276,6 +276,11 @@ class Plan:
         """Thin-level threshold of the hybrid mode (0 = automatic)."""
         L.check(L.lib().sptrsv_plan_set_thin_rows(self.p, int(thin_rows)), "sptrsv_plan_set_thin_rows")
 
+    def set_blocks_per_sm(self, blocks: int = 0):
+        """Resident blocks per SM of the level-persistent and hybrid grids
+        (0 = as many as fit)."""
+        L.check(L.lib().sptrsv_plan_set_blocks_per_sm(self.p, int(blocks)), "sptrsv_plan_set_blocks_per_sm")
+
     def withhold(self, row: int):
         L.check(L.lib().sptrsv_debug_withhold_row(self.p, row))
 

@@ -269,6 +269,27 @@ def test_hybrid_thin_thresholds(name):
     assert P.handle().status() == 0
 
 
+def test_persistent_grid_any_size():
+    """The level-persistent and hybrid solves with their persistent grids cut
+    to 1, 2 and 3 blocks per SM and back to the occupancy maximum: the same
+    results as the oracle (a row group only waits on groups taken before it,
+    so any grid completes)."""
+    import paper_2609_40159_gb300 as P
+    A_h = S.lap2d(97)
+    A = P.Matrix.from_host(A_h)
+    b_h = S.rhs(A_h.n, 1, seed=4)
+    b = torch.as_tensor(b_h).cuda()
+    x_ref = oracle.solve(A_h, b_h)
+    for mode in ("level", "hybrid"):
+        plan = P.Plan(A, mode=mode)
+        for bps in (1, 2, 3, 0):
+            plan.set_blocks_per_sm(bps)
+            assert relerr(plan.solve(b).cpu().numpy(), x_ref) <= 1e-12, (mode, bps)
+    with pytest.raises(P.SpTRSVError):
+        plan.set_blocks_per_sm(-1)
+    assert P.handle().status() == 0
+
+
 @pytest.mark.parametrize("mode", ["level", "syncfree", "block", "hybrid"])
 def test_column_major_multi_rhs(mode):
     """SpTRSM in the column-major layout (every right-hand side contiguous,
