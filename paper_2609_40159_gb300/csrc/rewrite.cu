@@ -78,6 +78,10 @@ __device__ __forceinline__ Ws warp_ws(char *base, int cap, int64_t wid)
     return w;
 }
 
+// Integer mixer for the open-addressing set: xor-shift / multiply rounds
+// with the published "lowbias32" constants of C. Wellons' hash-prospector
+// search (a well-mixed 32-bit bijection, so distinct keys never collide
+// before the table mask).
 __device__ __forceinline__ unsigned hash32(unsigned k)
 {
     k ^= k >> 16;
