@@ -116,3 +116,47 @@ def test_tune_batch_picks_the_level_schedule_where_it_pays(monkeypatch):
     assert fake.sched[:4] == ["level"] * 4
     assert fake.sched[4:] == ["inorder"] * 4
     assert {v["schedule"] for v in res["choice"].values()} == {"level", "inorder"}
+
+
+class _FakePlan:
+    """Stand-in single-system plan: the solve time of a (mode, rows per warp,
+    tile) choice is read from a table; the tuner must apply the table's
+    minimum."""
+
+    def __init__(self, times):
+        self.A = _Mat(10_000, 50_000, nlevels=100)
+        self.A.dtype = torch.float64
+        self.times = times
+        self.choice = None
+
+    def info(self):
+        return {"nlevels": self.A.nlevels}
+
+    def set(self, mode=0, rows_per_warp=0, rhs_tile=0):
+        self.choice = (mode, rows_per_warp, rhs_tile)
+
+    def solve(self, b, out=None):
+        return out
+
+
+def test_tune_plan_applies_the_fastest_candidate(monkeypatch):
+    """tune_plan (without its cache) times every mode x rows per warp x tile
+    candidate once and leaves the plan on the fastest one."""
+    rng = np.random.default_rng(0)
+    modes, rpws, kts = ("level", "syncfree", "block", "hybrid"), (1, 4, 32), (1, 4)
+    times = {(m, r, t): float(rng.uniform(1, 10)) for m in modes for r in rpws for t in kts}
+    times[("hybrid", 4, 1)] = 0.5
+    plan = _FakePlan(times)
+    seen = []
+
+    def tc(fn, reps=5):
+        fn()
+        seen.append(plan.choice)
+        return times[plan.choice]
+
+    monkeypatch.setattr(autotune, "time_call", tc)
+    res = autotune.tune_plan(plan, torch.zeros(10_000, 4, dtype=torch.float64), modes=modes, rpws=rpws,
+                             kts=kts, use_cache=False, reps=1)
+    assert sorted(seen) == sorted(times)
+    assert plan.choice == ("hybrid", 4, 1)
+    assert res["best"]["mode"] == "hybrid" and res["best"]["ms"] == 0.5 and not res["cached"]
